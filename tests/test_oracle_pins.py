@@ -1,0 +1,396 @@
+"""Pins of the FP64 CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values printed in the
+paper, closed forms, invariants, special cases that reduce to a textbook or library
+routine (numpy / scipy LAPACK), brute force on tiny inputs, or an independent
+implementation of a published definition (numpy's Philox).  None of them re-types the
+oracle's own arithmetic.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+from scipy import stats
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------
+# Alg. 2 step 2: s = 4 n log n, pinned by the seven sample sizes the paper prints
+# ---------------------------------------------------------------------------------------
+def test_sample_size_matches_paper(orc):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "sample_sizes.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 7
+    for n, s in rows:
+        assert orc.sample_size(int(n)) == int(s), (n, s)
+
+
+# ---------------------------------------------------------------------------------------
+# Philox4x64-10 (Salmon et al., SC'11) against numpy's independent implementation.
+# numpy increments its 256-bit counter before producing a block, so block t comes from a
+# generator started at counter t - 1.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("key", [(0, 0x5A4D504C), (12345, 0x5A4D504C), (2**64 - 1, 7)])
+@pytest.mark.parametrize("t", [0, 1, 2, 1000, 2**40 + 3])
+def test_philox_matches_numpy(orc, key, t):
+    ctr = (t - 1) % (1 << 256)
+    words = [(ctr >> (64 * i)) & ((1 << 64) - 1) for i in range(4)]
+    g = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(words, dtype=np.uint64))
+    ref = [int(v) for v in g.random_raw(4)]
+    assert orc.philox4x64_10((t, 0, 0, 0), key) == ref
+
+
+# ---------------------------------------------------------------------------------------
+# Eq. (R2P) and Alg. 2 step 1: the exact fixed-point weights against the plain formulas
+# ---------------------------------------------------------------------------------------
+def _dense_cases():
+    return [W.gaussian_dense(300, 17, 1)["A"],
+            W.udv_dense(500, 24, 1e4, 2)["A"],
+            np.ldexp(W.gaussian_dense(64, 9, 3)["A"], 200),   # large scale
+            np.ldexp(W.gaussian_dense(64, 9, 4)["A"], -300)]  # small scale
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_column_scales_equal_column_norms(orc, case):
+    A = _dense_cases()[case]
+    d2, d, inv, E1 = orc.col_scales({"kind": "dense", "A": A})
+    ref = (A * A).sum(axis=0)
+    np.testing.assert_allclose(d2, ref, rtol=1e-12)
+    np.testing.assert_allclose(d, np.linalg.norm(A, axis=0), rtol=1e-12)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_row_weights_equal_normalised_row_norms(orc, case):
+    A = _dense_cases()[case]
+    mat = {"kind": "dense", "A": A}
+    d2, d, inv, E1 = orc.col_scales(mat)
+    lo, hi = orc.row_weights(mat, inv)
+    w = np.array([float((int(h) << 64) | int(l)) for l, h in zip(lo, hi)])
+    p = w / w.sum()
+    Ah = A / np.linalg.norm(A, axis=0)
+    ref = (Ah * Ah).sum(axis=1) / A.shape[1]   # Eq. (R2P) on the normalised matrix: ||â_i||^2 / n
+    np.testing.assert_allclose(p, ref, rtol=1e-9, atol=1e-15)
+    # the normalised Frobenius norm is n (Sec. 4.1: ||A||_F^2 = n after normalisation)
+    assert abs(w.sum() / 2.0**51 - A.shape[1]) < 1e-9 * A.shape[1]
+
+
+def test_row_weights_raw_mode(orc):
+    A = _dense_cases()[1]
+    mat = {"kind": "dense", "A": A}
+    d2, d, inv, E1 = orc.col_scales(mat, normalize=False)
+    assert np.all(d == 1.0)
+    lo, hi = orc.row_weights(mat, inv)
+    w = np.array([float((int(h) << 64) | int(l)) for l, h in zip(lo, hi)])
+    ref = (A * A).sum(axis=1)
+    np.testing.assert_allclose(w / w.sum(), ref / ref.sum(), rtol=1e-9)
+
+
+def test_prefix_is_cumulative_sum(orc):
+    rng = np.random.default_rng(5)
+    lo = rng.integers(0, 2**63, size=50, dtype=np.uint64)
+    hi = rng.integers(0, 4, size=50, dtype=np.uint64)
+    P_lo, P_hi = orc.prefix(lo, hi)
+    vals = [(int(h) << 64) | int(l) for l, h in zip(lo, hi)]
+    acc = 0
+    for i in range(50):
+        assert (int(P_hi[i]) << 64) | int(P_lo[i]) == acc
+        acc += vals[i]
+    assert (int(P_hi[50]) << 64) | int(P_lo[50]) == acc
+
+
+# ---------------------------------------------------------------------------------------
+# Alg. 1 draws: special cases and the law of the draws
+# ---------------------------------------------------------------------------------------
+def test_single_nonzero_row_is_always_drawn(orc):
+    A = np.zeros((40, 5))
+    A[17] = [1.0, -2.0, 3.0, 0.5, 1.0]
+    smp = orc.Sample({"kind": "dense", "A": A}, seed=3, s=500)
+    assert np.all(smp.idx == 17)
+
+
+def test_coherent_Z_draws_only_identity_rows(orc):
+    # Sec. 3.1, matrix Z = [I_n; 0]: norm-squared sampling puts all mass on the first n
+    # rows, each with probability 1/n.
+    m, n = 200, 8
+    smp = orc.Sample(W.coherent_dense(m, n), seed=11, s=80000)
+    assert smp.idx.max() < n
+    counts = np.bincount(smp.idx, minlength=n)
+    chi2 = stats.chisquare(counts).pvalue
+    assert chi2 > 1e-4
+
+
+def test_zero_weight_rows_never_drawn_and_chi_square(orc):
+    rng = np.random.default_rng(7)
+    m, n = 60, 4
+    A = rng.standard_normal((m, n)) * rng.uniform(0.1, 3.0, size=(m, 1))
+    A[::7] = 0.0                                  # zero rows
+    smp = orc.Sample({"kind": "dense", "A": A}, seed=99, s=200000)
+    assert not np.isin(smp.idx, np.arange(0, m, 7)).any()
+    Ah = A / np.linalg.norm(A, axis=0)
+    p = (Ah * Ah).sum(1) / n                      # Eq. (R2P)
+    counts = np.bincount(smp.idx, minlength=m)
+    keep = p > 0
+    res = stats.chisquare(counts[keep], f_exp=p[keep] * smp.s)
+    assert res.pvalue > 1e-4, res
+
+
+def test_draws_reproduce_and_depend_on_seed(orc):
+    mat = W.gaussian_dense(1000, 10, 1)
+    a = orc.Sample(mat, seed=5).idx
+    b = orc.Sample(mat, seed=5).idx
+    c = orc.Sample(mat, seed=6).idx
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    # draw t does not depend on how many draws are taken (counter-based)
+    smp = orc.Sample(mat, seed=5)
+    assert smp.s == 93
+    tail = orc.draw_rows(smp.P_lo, smp.P_hi, 5, 10, t0=50)
+    assert np.array_equal(tail, smp.idx[50:60])
+
+
+# ---------------------------------------------------------------------------------------
+# Sec. 3.3: the sampled normal matrix
+# ---------------------------------------------------------------------------------------
+class _FullSample:
+    """Every row once with equal weights: then (1/s) sum_t â^T â / p = Â^T Â exactly."""
+
+    def __init__(self, orc, mat, normalize=True):
+        self.mat = orc.as_mat(mat)
+        self.d2, self.d, self.inv_d2, _ = orc.col_scales(self.mat, normalize)
+        m = self.mat.m
+        self.w_lo = np.ones(m, np.uint64)
+        self.w_hi = np.zeros(m, np.uint64)
+        self.idx = np.arange(m, dtype=np.int32)
+
+
+def test_full_sampling_gives_normalised_normal_matrix(orc):
+    A = W.gaussian_dense(50, 7, 8)["A"]
+    A[:, 3] *= 100.0
+    fs = _FullSample(orc, {"kind": "dense", "A": A})
+    M = orc.SampledM(fs).dense()
+    Ah = A / np.linalg.norm(A, axis=0)
+    np.testing.assert_allclose(M, Ah.T @ Ah, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(np.diag(M), 1.0, rtol=1e-12)
+
+
+def test_incidence_identity_laplacian(orc):
+    # Sec. 5.5: B^T B = D - A for an oriented incidence matrix, whatever the orientation.
+    rng = np.random.default_rng(3)
+    N = 12
+    edges = {(i, j) for i, j in rng.integers(0, N, size=(40, 2)) if i != j}
+    edges = sorted({(min(i, j), max(i, j)) for i, j in edges})
+    B = np.zeros((len(edges), N))
+    for e, (i, j) in enumerate(edges):
+        s = 1.0 if rng.random() < 0.5 else -1.0
+        B[e, i], B[e, j] = s, -s
+    fs = _FullSample(orc, W.csr_from_dense(B, keep_zeros=False), normalize=False)
+    M = orc.SampledM(fs).dense()
+    Adj = np.zeros((N, N))
+    for i, j in edges:
+        Adj[i, j] = Adj[j, i] = 1.0
+    Lap = np.diag(Adj.sum(1)) - Adj
+    deg0 = np.diag(Lap) == 0
+    Lap[deg0, deg0] = 1.0   # an isolated node has a zero diagonal, replaced by 1
+    np.testing.assert_allclose(M, Lap, atol=1e-12)
+
+
+def test_sampled_normal_matrix_is_unbiased(orc):
+    # Eq. (EATA): E[A_s^T A_s] = A^T A.  Monte Carlo over 400 seeds on a tiny matrix.
+    A = W.gaussian_dense(30, 4, 2)["A"] * np.linspace(0.2, 3, 30)[:, None]
+    mat = {"kind": "dense", "A": A}
+    Ah = A / np.linalg.norm(A, axis=0)
+    N = Ah.T @ Ah
+    reps = [orc.SampledM(orc.Sample(mat, seed=sd, s=12)).dense() for sd in range(400)]
+    mean = np.mean(reps, axis=0)
+    se = np.std(reps, axis=0) / np.sqrt(len(reps))
+    assert np.all(np.abs(mean - N) <= 5 * se + 1e-12)
+
+
+def test_unsampled_column_gets_unit_diagonal(orc):
+    A = np.zeros((10, 3))
+    A[:5, 0] = 1.0
+    A[5:, 1] = 2.0
+    A[9, 2] = 1e-30            # column 2 exists but is never drawn with these seeds/sizes
+    smp = orc.Sample({"kind": "dense", "A": A}, seed=1, s=4)
+    Mo = orc.SampledM(smp)
+    Md = Mo.dense()
+    if 9 not in smp.idx:
+        assert Md[2, 2] == 1.0 and Mo.n_fixed_diag == 1
+
+
+def test_sparse_and_dense_M_agree(orc):
+    mat = W.sparse_random(400, 30, 4, 9)
+    dense = {"kind": "dense", "A": W.dense_from_csr(mat)}
+    s1 = orc.Sample(mat, seed=4)
+    s2 = orc.Sample(dense, seed=4)
+    assert np.array_equal(s1.idx, s2.idx)   # zeros carry no weight: same law, same draws
+    M1 = orc.SampledM(s1).dense()
+    M2 = orc.SampledM(s2).dense()
+    np.testing.assert_allclose(M1, M2, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------
+# Alg. 3: the SGS preconditioner
+# ---------------------------------------------------------------------------------------
+def _spd(n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    return (Q * np.logspace(0, -np.log10(cond), n)) @ Q.T
+
+
+def _Mo(orc, Md):
+    n = Md.shape[0]
+    rows, cols = np.nonzero(np.ones_like(Md))
+    return orc.SampledM.from_csr(n, np.arange(0, n * n + 1, n), cols.astype(np.int32), Md.reshape(-1))
+
+
+def test_sgs_one_sweep_closed_form(orc):
+    # t = 1 from e0 = 0: e = B^{-T} D B^{-1} r with B the lower triangle (incl. diagonal)
+    Md = _spd(9, 1)
+    Mo = _Mo(orc, Md)
+    Bl = np.tril(Md)
+    D = np.diag(np.diag(Md))
+    P = sl.solve_triangular(Bl.T, D @ sl.solve_triangular(Bl, np.eye(9), lower=True), lower=False)
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        r = rng.standard_normal(9)
+        np.testing.assert_allclose(orc.sgs_apply(Mo, r, 1), P @ r, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("t", [1, 2, 5])
+def test_sgs_symmetric_positive_definite(orc, t):
+    Md = _spd(12, 3, cond=1e4)
+    Mo = _Mo(orc, Md)
+    P = np.column_stack([orc.sgs_apply(Mo, e, t) for e in np.eye(12)])
+    np.testing.assert_allclose(P, P.T, rtol=1e-9, atol=1e-9 * np.abs(P).max())
+    assert np.linalg.eigvalsh((P + P.T) / 2).min() > 0
+
+
+def test_sgs_many_sweeps_converge_to_inverse(orc):
+    # Gauss-Seidel converges for SPD matrices: t -> infinity gives M^{-1}
+    Md = _spd(8, 4, cond=10.0)
+    Mo = _Mo(orc, Md)
+    r = np.random.default_rng(1).standard_normal(8)
+    np.testing.assert_allclose(orc.sgs_apply(Mo, r, 200), np.linalg.solve(Md, r), rtol=1e-10)
+
+
+def test_sgs_diagonal_matrix_is_exact_inverse(orc):
+    d = np.array([2.0, 0.5, 4.0, 1.0])
+    Mo = _Mo(orc, np.diag(d))
+    r = np.array([1.0, -2.0, 3.0, 0.25])
+    np.testing.assert_allclose(orc.sgs_apply(Mo, r, 1), r / d, rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# The two products and PCG (Alg. 2 step 4)
+# ---------------------------------------------------------------------------------------
+def test_normal_matvec_matches_numpy(orc):
+    mat = W.sparse_random(300, 20, 5, 1)
+    A = W.dense_from_csr(mat)
+    d = np.linalg.norm(A, axis=0)
+    p = np.random.default_rng(0).standard_normal(20)
+    Ah = A / d
+    np.testing.assert_allclose(orc.normal_matvec(mat, d, p), Ah.T @ (Ah @ p), rtol=1e-12)
+
+
+@pytest.mark.parametrize("gen", ["gauss", "udv", "sparse", "semi"])
+def test_pcg_matches_lapack_least_squares(orc, gen):
+    if gen == "gauss":
+        mat = W.gaussian_dense(600, 20, 1)
+    elif gen == "udv":
+        mat = W.udv_dense(800, 16, 1e3, 2)
+    elif gen == "semi":
+        mat = W.semi_gaussian_dense(500, 16, 3)
+    else:
+        mat = W.sparse_random(900, 25, 6, 3)
+    A = mat["A"] if mat["kind"] == "dense" else W.dense_from_csr(mat)
+    xs, b = W.rhs_for(mat, 1, 1e-3, 4)
+    S = orc.Solve(mat, b[0], seed=10, tol=1e-12)
+    assert S.info["converged"] == 1
+    x_ref = np.linalg.lstsq(A, b[0], rcond=None)[0]                   # QR / SVD (LAPACK)
+    kappa2 = np.linalg.cond(A / np.linalg.norm(A, axis=0)) ** 2
+    assert np.linalg.norm(S.x - x_ref) / np.linalg.norm(x_ref) <= 10 * kappa2 * 1e-12
+    # also the Cholesky solve of the normal equation (Eq. NOR)
+    c = sl.cho_factor(A.T @ A)
+    x_ne = sl.cho_solve(c, A.T @ b[0])
+    assert np.linalg.norm(S.x - x_ne) / np.linalg.norm(x_ne) <= 10 * kappa2 * 1e-12
+    r = A.T @ (b[0] - A @ S.x)
+    assert np.linalg.norm(r) / np.linalg.norm(A.T @ b[0]) <= 1e-11
+
+
+def test_pcg_energy_error_decreases_monotonically(orc):
+    # CG minimises the A^T A-norm of the error over growing Krylov spaces.
+    mat = W.udv_dense(400, 12, 1e2, 5)
+    A = mat["A"]
+    xs, b = W.rhs_for(mat, 1, 0.0, 6)
+    smp = orc.Sample(mat, seed=3)
+    Mo = orc.SampledM(smp)
+    Ah = A / smp.d
+    N = Ah.T @ Ah
+    y_star = np.linalg.solve(N, Ah.T @ b[0])
+    errs = []
+    for k in range(1, 13):
+        y, info = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=1e-300, maxit=k, max_outer=1)
+        e = y - y_star
+        errs.append(e @ N @ e)
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-9) for i in range(len(errs) - 1))
+
+
+def test_pcg_terminates_in_n_steps_when_well_conditioned(orc):
+    # exact arithmetic terminates in at most n steps; FP64 on a well-conditioned problem
+    # gets there up to rounding
+    mat = W.udv_dense(400, 12, 3.0, 5)
+    A = mat["A"]
+    xs, b = W.rhs_for(mat, 1, 0.0, 6)
+    smp = orc.Sample(mat, seed=3)
+    Mo = orc.SampledM(smp)
+    Ah = A / smp.d
+    N = Ah.T @ Ah
+    y_star = np.linalg.solve(N, Ah.T @ b[0])
+    y0, _ = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=1e-300, maxit=1, max_outer=1)
+    y, _ = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=1e-300, maxit=12, max_outer=1)
+    e0, e = y0 - y_star, y - y_star
+    assert e @ N @ e <= 1e-24 * (e0 @ N @ e0)
+
+
+def test_pcg_iteration_count_zero_for_zero_rhs(orc):
+    mat = W.gaussian_dense(100, 5, 1)
+    S = orc.Solve(mat, np.zeros(100), seed=1)
+    assert S.info["iters"] == 0 and S.info["converged"] == 1 and np.all(S.x == 0)
+
+
+# ---------------------------------------------------------------------------------------
+# Adjoint: dL/db = A lam, dL/dA = r lam^T - (A lam) x^T with A^T A lam = dL/dx
+# ---------------------------------------------------------------------------------------
+def test_adjoint_matches_closed_form_and_finite_differences(orc):
+    mat = W.gaussian_dense(80, 6, 2)
+    A = mat["A"]
+    xs, b = W.rhs_for(mat, 1, 1e-1, 3)
+    b = b[0]
+    target = np.random.default_rng(1).standard_normal(6)
+
+    def loss(Am, bm):
+        S = orc.Solve({"kind": "dense", "A": Am}, bm, seed=2, tol=1e-14)
+        return np.sum((S.x - target) ** 2), S
+
+    L0, S = loss(A, b)
+    G = 2 * (S.x - target)
+    gb, gA, lam, info = orc.adjoint(mat, S.smp, S.M, S.x, b, G, tol=1e-14)
+    lam_ref = np.linalg.solve(A.T @ A, G)
+    np.testing.assert_allclose(lam, lam_ref, rtol=1e-9)
+    r = b - A @ S.x
+    np.testing.assert_allclose(gA, np.outer(r, lam_ref) - np.outer(A @ lam_ref, S.x), rtol=1e-8, atol=1e-12)
+    h = 1e-6
+    for i in [0, 17, 79]:
+        e = np.zeros_like(b)
+        e[i] = h
+        fd = (loss(A, b + e)[0] - loss(A, b - e)[0]) / (2 * h)
+        assert abs(fd - gb[i]) <= 1e-6 * max(1.0, abs(gb[i]))
+    for (i, j) in [(0, 0), (40, 3), (79, 5)]:
+        E = np.zeros_like(A)
+        E[i, j] = h
+        fd = (loss(A + E, b)[0] - loss(A - E, b)[0]) / (2 * h)
+        assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))

@@ -1,0 +1,204 @@
+"""Seeded synthetic inputs for the row-sampling SGS-preconditioned PCG least-squares solver.
+
+This module only draws random matrices and right-hand sides; it holds none of the
+method's arithmetic (no norms, no sampling, no preconditioner, no solve).  Both the
+CPU oracle's tests and the CUDA path's tests and benchmark take their inputs from
+here, so that the two sides see the same bits.
+
+Every generator is a pure function of its arguments (numpy ``default_rng(seed)``),
+returns host numpy arrays, and describes its matrix as either
+
+* dense:  ``{"kind": "dense", "A": (m, n) float64 C-contiguous}``
+* CSR:    ``{"kind": "csr", "m", "n", "row_ptr": int64[m+1], "col_idx": int32[nnz],
+            "vals": float64[nnz]}`` with strictly increasing columns inside a row.
+
+The workload families follow the paper's experiment classes (Section 5): Gaussian
+(5.1), UDV (5.4), sparse random (5.3) and graph incidence (5.5), at the sizes of the
+solver's benchmark configurations.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "gaussian_dense", "udv_dense", "semi_gaussian_dense", "coherent_dense",
+    "sparse_random", "graph_incidence", "rhs_for", "uneven_dense_batch",
+    "csr_from_dense", "dense_from_csr",
+]
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def gaussian_dense(m: int, n: int, seed: int) -> dict:
+    """A = randn(m, n): i.i.d. N(0,1) entries (Section 5.1, Gaussian matrix)."""
+    A = _rng(seed).standard_normal((m, n))
+    return {"kind": "dense", "A": np.ascontiguousarray(A)}
+
+
+def udv_dense(m: int, n: int, kappa: float, seed: int, qr=None) -> dict:
+    """A = U diag(sigma) V^T (Section 5.4, UDV matrix).
+
+    U is the orthonormal Q factor of a seeded Gaussian m x n, V the Q factor of a
+    seeded Gaussian n x n, and sigma is log-spaced from 1 down to 1/kappa, so that
+    kappa(A) = kappa.  ``qr`` may be a callable (G -> Q) used for the large QR
+    (for example a device QR); by default numpy's LAPACK QR is used.
+    """
+    rng = _rng(seed)
+    G = rng.standard_normal((m, n))
+    H = rng.standard_normal((n, n))
+    qr = qr or (lambda X: np.linalg.qr(X, mode="reduced")[0])
+    U = np.asarray(qr(G), dtype=np.float64)
+    V = np.linalg.qr(H, mode="reduced")[0]
+    sigma = np.logspace(0.0, -math.log10(kappa), n)
+    A = (U * sigma[None, :]) @ V.T
+    return {"kind": "dense", "A": np.ascontiguousarray(A), "sigma": sigma}
+
+
+def semi_gaussian_dense(m: int, n: int, seed: int) -> dict:
+    """[B 0; 0 I_{n/2}] with B Gaussian (m - n/2) x n/2 (Section 5.2, coherent)."""
+    h = n // 2
+    A = np.zeros((m, n))
+    A[: m - (n - h), :h] = _rng(seed).standard_normal((m - (n - h), h))
+    A[m - (n - h):, h:] = np.eye(n - h)
+    return {"kind": "dense", "A": A}
+
+
+def coherent_dense(m: int, n: int) -> dict:
+    """Z = [I_n; 0] (Section 3.1, the fully coherent example)."""
+    A = np.zeros((m, n))
+    A[:n, :n] = np.eye(n)
+    return {"kind": "dense", "A": A}
+
+
+def _csr_from_coo(m, n, rows, cols, vals):
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    counts = np.bincount(rows, minlength=m)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return {"kind": "csr", "m": int(m), "n": int(n), "row_ptr": row_ptr,
+            "col_idx": cols.astype(np.int32), "vals": vals.astype(np.float64)}
+
+
+def sparse_random(m: int, n: int, nnz_per_row: int, seed: int,
+                  log10_scale: float = 2.0) -> dict:
+    """Sparse random CSR in the spirit of the paper's ``sprand`` tests (Section 5.3).
+
+    Each row has ``nnz_per_row`` distinct uniform random columns; every column j gets
+    one extra entry at a uniform random row (skipped if already present), so that no
+    column is empty.  Values are N(0,1) times a per-row scale 10^U(-s, s) with
+    s = ``log10_scale`` (rows of very different norms, which the norm-squared
+    sampling density is designed for).
+    """
+    rng = _rng(seed)
+    k = nnz_per_row
+    cols = rng.integers(0, n, size=(m, k), dtype=np.int64)
+    # redraw duplicates inside a row until every row has k distinct columns
+    while True:
+        s = np.sort(cols, axis=1)
+        dup_rows = np.nonzero((s[:, 1:] == s[:, :-1]).any(axis=1))[0]
+        if dup_rows.size == 0:
+            break
+        cols[dup_rows] = rng.integers(0, n, size=(dup_rows.size, k), dtype=np.int64)
+    rows = np.repeat(np.arange(m, dtype=np.int64), k)
+    cols = cols.reshape(-1)
+    extra_rows = rng.integers(0, m, size=n, dtype=np.int64)
+    extra_cols = np.arange(n, dtype=np.int64)
+    key = rows * n + cols
+    present = np.isin(extra_rows * n + extra_cols, key)
+    rows = np.concatenate([rows, extra_rows[~present]])
+    cols = np.concatenate([cols, extra_cols[~present]])
+    scale = 10.0 ** rng.uniform(-log10_scale, log10_scale, size=m)
+    vals = rng.standard_normal(rows.size) * scale[rows]
+    return _csr_from_coo(m, n, rows, cols, vals)
+
+
+def graph_incidence(n_nodes: int, n_edges: int, seed: int,
+                    log10_w: float = 3.0) -> dict:
+    """Weighted incidence matrix of a random connected graph (Section 5.5).
+
+    ``n_edges`` edges with uniform random endpoints (self-loops redrawn, duplicate
+    edges allowed) plus a spanning path over a seeded random permutation of the
+    nodes, so the graph is connected.  Edge e with weight w_e = 10^U(-3,3) gives a
+    row with +sqrt(w_e) at its source and -sqrt(w_e) at its target.  Node 0 is
+    grounded (its column removed), so the matrix has full column rank n_nodes - 1.
+    """
+    rng = _rng(seed)
+    src = rng.integers(0, n_nodes, size=n_edges, dtype=np.int64)
+    dst = rng.integers(0, n_nodes, size=n_edges, dtype=np.int64)
+    while True:
+        loops = np.nonzero(src == dst)[0]
+        if loops.size == 0:
+            break
+        dst[loops] = rng.integers(0, n_nodes, size=loops.size, dtype=np.int64)
+    perm = rng.permutation(n_nodes).astype(np.int64)
+    src = np.concatenate([src, perm[:-1]])
+    dst = np.concatenate([dst, perm[1:]])
+    m = src.size
+    w = 10.0 ** rng.uniform(-log10_w, log10_w, size=m)
+    sw = np.sqrt(w)
+    rows = np.concatenate([np.arange(m), np.arange(m)])
+    cols = np.concatenate([src, dst])
+    vals = np.concatenate([sw, -sw])
+    keep = cols != 0
+    return _csr_from_coo(m, n_nodes - 1, rows[keep], cols[keep] - 1, vals[keep])
+
+
+def rhs_for(mat: dict, k: int, noise: float, seed: int):
+    """x* ~ N(0,1) (n x k) and b = A x* + noise * N(0,1) (m x k), column-major blocks.
+
+    Returns (xstar, b) as float64 arrays of shape (k, n) and (k, m): row c of each is
+    right-hand side / solution number c, contiguous.
+    """
+    rng = _rng(seed)
+    if mat["kind"] == "dense":
+        m, n = mat["A"].shape
+    else:
+        m, n = mat["m"], mat["n"]
+    xstar = rng.standard_normal((k, n))
+    if mat["kind"] == "dense":
+        Ax = (mat["A"] @ xstar.T).T
+    else:
+        Ax = np.empty((k, m))
+        rp, ci, v = mat["row_ptr"], mat["col_idx"], mat["vals"]
+        rows = np.repeat(np.arange(m), np.diff(rp))
+        for c in range(k):
+            Ax[c] = np.bincount(rows, weights=v * xstar[c][ci], minlength=m)
+    b = Ax + noise * rng.standard_normal((k, m))
+    return np.ascontiguousarray(xstar), np.ascontiguousarray(b)
+
+
+def uneven_dense_batch(count: int, m_range, n_range, seed: int):
+    """``count`` dense Gaussian problems with m, n drawn log-uniform in the ranges."""
+    rng = _rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(round(math.exp(rng.uniform(math.log(m_range[0]), math.log(m_range[1])))))
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        n = min(n, m)
+        out.append({"kind": "dense", "A": rng.standard_normal((m, n))})
+    return out
+
+
+def csr_from_dense(A: np.ndarray, keep_zeros: bool = True) -> dict:
+    """CSR view of a dense matrix (all entries stored when ``keep_zeros``)."""
+    m, n = A.shape
+    if keep_zeros:
+        rows = np.repeat(np.arange(m, dtype=np.int64), n)
+        cols = np.tile(np.arange(n, dtype=np.int64), m)
+        vals = A.reshape(-1)
+    else:
+        rows, cols = np.nonzero(A)
+        vals = A[rows, cols]
+    return _csr_from_coo(m, n, rows.astype(np.int64), cols.astype(np.int64), vals)
+
+
+def dense_from_csr(mat: dict) -> np.ndarray:
+    A = np.zeros((mat["m"], mat["n"]))
+    rows = np.repeat(np.arange(mat["m"]), np.diff(mat["row_ptr"]))
+    np.add.at(A, (rows, mat["col_idx"]), mat["vals"])
+    return A

@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-1e-10 solve of the row-sampling SGS-preconditioned PCG method.
+
+One step = one pass of the whole hot path over one problem: exact column scales, row
+weights, prefix and Philox draws (lsq_sample_rows), sampled normal matrix and SGS operator
+(lsq_build_precond), and PCG with true-residual restarts to a relative normal-equation
+residual of 1e-10 (lsq_pcg_solve).  The workload is the ill-conditioned dense UDV problem:
+A = U diag(sigma) V^T, 262144 x 512, sigma log-spaced from 1 to 1e-6 (kappa(A) = 1e6),
+b = A x* + 1e-6 noise, s = ceil(4 n ln n) = 12777 draws, one forward + one backward sweep.
+A (1 GiB in FP64) is larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle (the method as
+written, FP64, single thread) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 solve and HBM GB/s of Ap/Aᵀq/SGS; mixed/batched/adjoint vs FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["f64", "f32"], default="f64",
+                    help="f64: FP64 values; f32: FP32 values + FP64 refinement")
+    ap.add_argument("--m", type=int, default=262144)
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--kappa", type=float, default=1e6)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--maxit", type=int, default=1000000)
+    ap.add_argument("--inner-tol", type=float, default=0.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.stop_ev = threading.Event()
+        self.th = None
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self.stop_ev.wait(0.2)
+
+    def start(self):
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+
+    def stop(self):
+        self.stop_ev.set()
+        if self.th:
+            self.th.join(timeout=10)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 4 + k and r[4 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def make_problem(args, seed_base, device_qr=True):
+    import workloads as W
+    qr = None
+    if device_qr:
+        import torch
+        qr = lambda G: torch.linalg.qr(torch.from_numpy(G).cuda())[0].cpu().numpy()
+    mat = W.udv_dense(args.m, args.n, args.kappa, seed_base, qr=qr)
+    xs, b = W.rhs_for(mat, 1, 1e-6, seed_base + 100)
+    return mat, xs[0], b[0]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+def pcg_algorithmic(args, m, n, info, es, es_res, es_op):
+    """Algorithmic bytes and flops of one lsq_pcg_solve launch (one column)."""
+    it = int(info.iters[0])
+    outer = int(info.outer[0])
+    a_bytes = m * n * es
+    per_iter = a_bytes + n * n * es_op                  # one pass over A, one over the operator
+    res_passes = 1 + max(outer - 1, 0) + 1              # h = Â^T b, restarts, final check
+    byts = it * per_iter + res_passes * (m * n * es_res + 8 * m)
+    flops = it * (4.0 * m * n + 2.0 * n * n) + res_passes * 4.0 * m * n
+    return byts, flops
+
+
+def cpu_oracle_sample(mat, b, seed, iters_gpu, cpu_iters):
+    """Oracle (FP64, one thread) on a bounded sample of one solve: full setup (S1-S6) plus
+    `cpu_iters` PCG iterations, extrapolated to the iteration count of a full solve."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    smp = oracle.Sample(mat, seed)
+    Mo = oracle.SampledM(smp)
+    t1 = time.perf_counter()
+    oracle.pcg(smp.mat, smp.d, Mo, b=b, tol=1e-300, maxit=cpu_iters, max_outer=1)
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / cpu_iters
+    t_solve = (t1 - t0) + per_iter * max(iters_gpu, 1)
+    return t_solve, (t1 - t0), per_iter
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    mat, xs, b = make_problem(args, 2, device_qr=False)
+    seed = 1002
+    times = []
+    iters_assumed = int(os.environ.get("LSQ_REF_ITERS", "193526"))
+    for k in range(args.warmup + args.steps):
+        t, ts, ti = cpu_oracle_sample(mat, b, seed, iters_assumed, args.cpu_iters)
+        if k >= args.warmup:
+            times.append(t)
+    t = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"udv_dense_{args.m}x{args.n}_kappa{args.kappa:g}",
+                       "tol": args.tol, "sweeps": 1, "s": math.ceil(4 * args.n * math.log(args.n))},
+            "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle setup (sampling, A_s^T A_s, SGS) on the full matrix + "
+                                       f"{args.cpu_iters} PCG iterations per step, extrapolated to "
+                                       f"{iters_assumed} iterations"},
+            "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1806_02968_gb300 as pkg
+    if rank == 0:
+        pkg.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1806_02968_gb300 import api
+
+    seed_base = 2 + rank                     # independent replica per rank (weak scaling)
+    mat, xs, b = make_problem(args, seed_base)
+    m, n = mat["A"].shape
+    A64 = torch.from_numpy(mat["A"]).cuda()
+    bd = torch.from_numpy(b).cuda()
+    if args.mode == "f64":
+        Mx = api.Matrix(A64)
+        es, es_res, es_op, pdt, dtype = 8, 8, 8, 0, "f64"
+    else:
+        A32 = A64.float()
+        Mx = api.Matrix(A32, vals_f64=A64)
+        es, es_res, es_op, pdt, dtype = 4, 8, 4, 1, "f32+f64"
+    o = api.opts(seed=1002 + rank, tol=args.tol, maxit=args.maxit, precond_dtype=pdt,
+                 inner_tol=args.inner_tol, max_outer=50)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        idx, p, d = api.lsq_sample_rows(Mx, o)
+        P = api.lsq_build_precond(Mx, idx, p, d, o)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = api.lsq_pcg_solve(Mx, P, bd, o)
+        e1.record(stream)
+        return x, info, (e0, e1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    L0 = api.launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    pcg_ms, infos = [], []
+    for _ in range(args.steps):
+        x, info, (e0, e1) = step()
+        infos.append(info)
+        e1.synchronize()
+        pcg_ms.append(e0.elapsed_time(e1))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = api.launches() - L0
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms = float(tmax.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    info = infos[-1]
+    byts, flops = pcg_algorithmic(args, m, n, info, es, es_res, es_op)
+    pcg_s = float(np.mean(pcg_ms)) / 1e3
+    pk = peaks()
+    if args.mode == "f64":
+        # FP64 FMA throughput bounds the fused pass on GB300 (2 FMAs per element of A per
+        # iteration); the nominal FP64 rate 1.25 TFLOP/s is the denominator
+        roof = {"bound": "alu", "achieved": flops / pcg_s / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": flops / pcg_s / 1e12 / 1.25, "traffic": None,
+                "hbm_gbs": byts / pcg_s / 1e9, "hbm_frac_of_measured": byts / pcg_s / 1e9 / pk["hbm_gbs"]}
+    else:
+        roof = {"bound": "hbm", "achieved": byts / pcg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": byts / pcg_s / 1e9 / pk["hbm_gbs"], "traffic": None}
+    roof["kernel"] = "k_pcg_dense"
+    roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (measured)" if args.mode != "f64" else \
+        "nominal FP64 rate (152 SMs x 2 FMA/clk x 2.07 GHz); measured FMA probe 1.19 TFLOP/s"
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        hA = torch.empty_like(A64, device="cpu").pin_memory()
+        hA.copy_(A64.cpu())
+        hb = torch.from_numpy(b).pin_memory()
+        hx = torch.empty(n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        dA = hA.to("cuda", non_blocking=True)
+        db = hb.to("cuda", non_blocking=True)
+        if args.mode == "f64":
+            Mh = api.Matrix(dA)
+        else:
+            Mh = api.Matrix(dA.float(), vals_f64=dA)
+        idx, p, d = api.lsq_sample_rows(Mh, o)
+        P = api.lsq_build_precond(Mh, idx, p, d, o)
+        xe, _ = api.lsq_pcg_solve(Mh, P, db, o)
+        hx.copy_(xe, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s0.elapsed_time(s1)
+        e2e = {"value": 1e3 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": int(hA.numel() * 8 + hb.numel() * 8),
+               "d2h_bytes_per_step": int(n * 8)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        t_solve, t_setup, t_iter = cpu_oracle_sample(mat, b, 1002, int(info.iters[0]), args.cpu_iters)
+        cpu = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle setup (sampling, A_s^T A_s, SGS) on the full matrix "
+                         f"({t_setup:.2f} s) + {args.cpu_iters} PCG iterations ({t_iter:.3f} s each), "
+                         f"extrapolated to the GPU's {int(info.iters[0])} iterations"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+                "data": "synthetic",
+                "config": {"workload": f"udv_dense_{m}x{n}_kappa{args.kappa:g}", "m": m, "n": n,
+                           "kappa": args.kappa, "tol": args.tol, "sweeps": 1, "s": int(info.s),
+                           "mode": args.mode, "l2": "inputs larger than L2 (A is %.2f GB)" % (m * n * es / 1e9),
+                           "parallelism": f"replicas{world}"},
+                "clocks": ck, "gpu_launches": int(launches),
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "solve": {"iters": int(info.iters[0]), "outer": int(info.outer[0]),
+                          "relres_true": float(info.relres_true[0]),
+                          "relres_raw": float(info.relres_raw[0]),
+                          "converged": int(info.converged[0]), "pcg_ms": float(np.mean(pcg_ms)),
+                          "us_per_iter": 1e3 * float(np.mean(pcg_ms)) / max(int(info.iters[0]), 1)}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

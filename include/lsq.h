@@ -1,0 +1,244 @@
+/*
+ * lsq.h -- C ABI of the GB300 (sm_103a) row-sampling SGS-preconditioned PCG solver for
+ * overdetermined least squares, after Chen & Wu, "A Preconditioner based on Non-uniform
+ * Row Sampling for Linear Least Squares Problems" (arXiv:1806.02968).
+ *
+ * Problem (Sec. 1, Eqs. AXB, OPT, NOR): A in R^{m x n}, m >> n, rank n, b in R^m;
+ * find x_opt = argmin ||A x - b||_2, i.e. solve A^T A x = A^T b.
+ *
+ * Method (Alg. 2):
+ *   1. normalise A <- A D^{-1}, D_jj = ||a^j||_2                 (lsq_sample_rows)
+ *   2. draw s = ceil(4 n ln n) rows i.i.d. with p_i = ||â_i||^2 / n (Alg. 1, Eq. R2P)
+ *                                                                (lsq_sample_rows)
+ *   3. build A_s^T A_s = (1/s) sum_t â_{i_t}^T â_{i_t} / p_{i_t}  (Sec. 3.3) and the
+ *      symmetric Gauss-Seidel preconditioner on it (Alg. 3)      (lsq_build_precond)
+ *   4. PCG on A^T A x = A^T b until the relative residual < eps  (lsq_pcg_solve)
+ * plus the adjoint solve used for gradients                       (lsq_pcg_adjoint).
+ *
+ * Conventions for every call:
+ *   - Pointers named "device" must point to device memory of the current CUDA device;
+ *     "host" pointers to host memory.  All array arguments are BORROWED: the caller owns
+ *     them and they must stay valid until the call returns (or, for stream-ordered
+ *     outputs, until the stream reaches that point).  The library never frees them.
+ *   - The only library-owned object is lsq_precond (free it with lsq_precond_destroy).
+ *     Per-call scratch is taken with cudaMallocAsync on the given stream and released on
+ *     the same stream before the call returns.
+ *   - Work is issued on the given stream (0 = legacy default stream).  Calls that report
+ *     data-dependent status (every call below) synchronise that stream once at the end
+ *     to read it.
+ *   - Errors are returned, never raised or aborted on: invalid shapes, dtypes, NULL
+ *     pointers or misaligned buffers give LSQ_ERR_INVALID; a failing CUDA call gives
+ *     LSQ_ERR_CUDA (lsq_last_error_string() has the CUDA message).  Device-side waits
+ *     (grid barriers) give up after a bounded number of polls and report LSQ_ERR_TIMEOUT.
+ *   - Sampling indices are a deterministic function of (A's values, seed, s); for a
+ *     given input the solver's floating-point results are deterministic as well (every
+ *     reduction has a fixed order).
+ */
+#ifndef LSQ_H
+#define LSQ_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSQ_API __attribute__((visibility("default")))
+#else
+#define LSQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSQ_OK = 0,
+    LSQ_ERR_INVALID = 1,        /* bad argument: shape, dtype, NULL, alignment, range */
+    LSQ_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    LSQ_ERR_NOMEM = 3,          /* device allocation failed */
+    LSQ_ERR_NOT_CONVERGED = 4,  /* maxit reached; outputs hold the last iterate */
+    LSQ_ERR_BREAKDOWN = 5,      /* PCG scalar rho <= 0, p^T w <= 0 or not finite */
+    LSQ_ERR_TIMEOUT = 6,        /* a device-side wait gave up (bounded spin) */
+    LSQ_ERR_UNSUPPORTED = 7     /* valid request this build does not implement */
+} lsq_status;
+
+/* Storage type of matrix values.  LSQ_F32X2 holds each value as an unevaluated sum of
+ * two floats (hi, lo), interleaved: element e occupies floats [2e, 2e+1]. */
+typedef enum { LSQ_F64 = 0, LSQ_F32 = 1, LSQ_BF16 = 2, LSQ_F32X2 = 3 } lsq_dtype;
+
+/* A in R^{m x n} (Sec. 1).  Dense: row-major, element (i, j) at vals[i*ld + j], ld >= n.
+ * CSR: row_ptr[m+1] (int64), col_idx[nnz] (int32, strictly increasing inside a row),
+ * vals[nnz].  All arrays are device memory.  vals_f64 (optional, NULL if absent) is an
+ * FP64 copy of the values in the same layout; when given with a lower-precision dtype,
+ * the solver computes its true residuals (iterative-refinement steps) from it. */
+typedef struct {
+    int64_t m, n, nnz;
+    int32_t dense;               /* 1 = dense row-major, 0 = CSR */
+    int64_t ld;                  /* dense leading dimension in elements */
+    const int64_t* row_ptr;      /* CSR, device, m+1 entries */
+    const int32_t* col_idx;      /* CSR, device, nnz entries */
+    const void* vals;            /* device, dtype as below */
+    int32_t dtype;               /* lsq_dtype */
+    const double* vals_f64;      /* optional device FP64 copy of vals (same layout) */
+} lsq_matrix;
+
+/* Options.  lsq_default_opts() fills the defaults shown. */
+typedef struct {
+    double tol;            /* relative residual tolerance eps (Alg. 2 step 4); 1e-10 */
+    int32_t maxit;         /* cap on PCG iterations over all outer steps; 1000000 */
+    int32_t max_outer;     /* cap on PCG (re)starts from the true residual; 20 */
+    int32_t sweeps;        /* t of Alg. 3 (forward and backward sweeps each); 1 */
+    double sample_factor;  /* C in s = ceil(C n ln n) (Alg. 2 step 2); 4.0 */
+    int32_t normalize;     /* Alg. 2 step 1 on (1) or off (0); 1 */
+    int32_t precond_dtype; /* LSQ_F64 or LSQ_F32: storage/arithmetic of the SGS operator */
+    uint64_t seed;         /* Philox key word for the draws of Alg. 1; 0 */
+    double inner_tol;      /* refinement form only: relative tolerance of each inner
+                              solve; 0 = tol (no separate inner tolerance) */
+    int32_t grid_ctas;     /* 0 = one persistent CTA per SM (x occupancy); else a cap */
+} lsq_opts;
+
+/* Per-right-hand-side results, written to caller-owned HOST arrays of length k (any
+ * pointer may be NULL).  relres_rec: recursive ||g||/||g0|| of the normalised normal
+ * equation; relres_true: the same recomputed from D^{-1} A^T (b - A x); relres_raw:
+ * ||A^T (b - A x)|| / ||A^T b|| without column scaling. */
+typedef struct {
+    int64_t k;
+    int32_t* iters;
+    int32_t* outer;
+    double* relres_rec;
+    double* relres_true;
+    double* relres_raw;
+    uint8_t* converged;
+    /* filled for the whole call */
+    int64_t s, nnz_M, n_fixed_diag, levels;
+    double setup_ms, solve_ms;
+} lsq_info;
+
+typedef struct lsq_precond lsq_precond;
+
+/* Defaults listed in lsq_opts. */
+LSQ_API void lsq_default_opts(lsq_opts* o);
+
+/* Alg. 2 step 2: s = ceil(C n ln n) (natural log, rounded up; Alg. 2 writes 4 n log n
+ * and the paper's printed sample sizes pin the natural log and the ceiling). */
+LSQ_API int64_t lsq_sample_size(int64_t n, double C);
+
+/*
+ * lsq_sample_rows -- Alg. 2 steps 1-2 and Alg. 1 with the density of Eq. (R2P).
+ *
+ * Computes the column scales d_j = ||a^j|| and draws s row indices i.i.d. with
+ * probability p_i = ||a_i D^{-1}||^2 / ||A D^{-1}||_F^2 (or ||a_i||^2/||A||_F^2 when
+ * o->normalize == 0).  The law is evaluated exactly in integers so that the indices
+ * are reproducible bit for bit:
+ *   t_ij = fl(a_ij^2) (FP64, one rounding), E1 = 52 - floor(log2 max t_ij),
+ *   c_j = sum_i floor(t_ij 2^E1) (exact), d2_j = RNE(c_j) 2^-E1, d_j = sqrt(d2_j);
+ *   w_i = sum_j floor(2^51 fl(t_ij fl(1/d2_j))) (exact), p_i = w_i / W, W = sum w_i;
+ *   draw t: Philox4x64-10 with key (seed, 0x5A4D504C), counter (t,0,0,0) -> words
+ *   (r0, r1, ...); U = r1 2^64 + r0; i_t = max{i : sum_{l<i} w_l <= floor(U W / 2^128)}.
+ * A column with c_j = 0 keeps d_j = 1 and no sampling weight.  max a_ij^2 must lie in
+ * [2^-900, 2^900] and every value must be finite (else LSQ_ERR_INVALID).
+ *
+ *   A          matrix (device arrays), any dtype
+ *   o          options (normalize, seed, sample_factor); host
+ *   s          number of draws; 0 means lsq_sample_size(n, o->sample_factor)
+ *   idx_out    device int32[s]: i_t in draw order (output)
+ *   p_out      device double[s]: p_{i_t} = w_{i_t}/W rounded to FP64 (output, may be NULL)
+ *   colscale_out device double[n]: d_j (output, may be NULL)
+ *   s_out      host: the s actually used (may be NULL)
+ *   stream     cudaStream_t as void*
+ */
+LSQ_API lsq_status lsq_sample_rows(const lsq_matrix* A, const lsq_opts* o, int64_t s,
+                           int32_t* idx_out, double* p_out, double* colscale_out,
+                           int64_t* s_out, void* stream);
+
+/*
+ * lsq_build_precond -- Sec. 3.3 and Alg. 3.
+ *
+ * Assembles M = A_s^T A_s = (1/s) sum_t â_{i_t}^T â_{i_t} / p_{i_t} (â = a D^{-1},
+ * duplicates of a row counted once per draw), replaces a zero diagonal entry by 1, and
+ * prepares the SGS operator of Alg. 3 with t = o->sweeps: e = 0; t forward corrections
+ * e <- e + B^{-1}(r - M e), B the lower triangle of M with its diagonal; then t backward
+ * corrections with B^T.  For dense A (n <= 2048) the operator is materialised once as an
+ * n x n matrix by running exactly those sweeps on the unit vectors, so that applying it
+ * inside PCG is one parallel product.
+ *
+ *   A, idx, p, colscale  as produced by lsq_sample_rows (device)
+ *   s          number of draws in idx/p
+ *   o          options (sweeps, precond_dtype); host
+ *   P_out      host: receives the new library-owned handle
+ */
+LSQ_API lsq_status lsq_build_precond(const lsq_matrix* A, const int32_t* idx, const double* p,
+                             const double* colscale, int64_t s, const lsq_opts* o,
+                             lsq_precond** P_out, void* stream);
+
+/* Free a handle from lsq_build_precond (NULL is ignored).  Stream-ordered on the stream
+ * the handle was built on. */
+LSQ_API void lsq_precond_destroy(lsq_precond* P);
+
+/* Copy the assembled M = A_s^T A_s out of a handle (dense: row-major n x n into M_out,
+ * device double[n*n]).  For checking and diagnostics. */
+LSQ_API lsq_status lsq_precond_get_M(const lsq_precond* P, double* M_out, void* stream);
+
+/* Copy the materialised SGS operator (dense handles only, row-major n x n, device
+ * double[n*n], converted to FP64). */
+LSQ_API lsq_status lsq_precond_get_op(const lsq_precond* P, double* op_out, void* stream);
+
+/* Apply the preconditioner of Alg. 3: e = P r for k vectors (device, column c at
+ * r + c*n, e + c*n). */
+LSQ_API lsq_status lsq_precond_apply(const lsq_precond* P, const double* r, double* e, int64_t k,
+                             void* stream);
+
+/*
+ * lsq_pcg_solve -- Alg. 2 step 4: PCG on A^T A x = A^T b with the preconditioner P.
+ *
+ * Works on the normalised system Â^T Â y = Â^T b, Â = A D^{-1}, x = D^{-1} y.  Textbook
+ * PCG from y = 0: g = Â^T b, z = P g, p = z; each iteration w = Â^T(Â p) in one fused
+ * pass over the rows of A, alpha = rho / ||Â p||^2, y += alpha p, g -= alpha w, stop when
+ * ||g|| <= tol ||Â^T b||, z = P g, beta = rho'/rho, p = z + beta p.  On stop the true
+ * residual Â^T (b - Â y) is recomputed (in FP64 from vals_f64 when given); if it misses
+ * the tolerance PCG restarts from y (one outer step), up to o->max_outer times.  The whole
+ * loop runs inside one persistent cooperative kernel.
+ *
+ *   A      matrix (device)
+ *   P      handle built for this A
+ *   B      device double, k right-hand sides, column c at B + c*ldb (ldb >= m)
+ *   X      device double, k solutions, column c at X + c*ldx (ldx >= n) (output)
+ *   info   host (may be NULL); per-column arrays of length >= k
+ * Returns LSQ_ERR_NOT_CONVERGED when some column misses the tolerance (X holds the last
+ * iterate), LSQ_ERR_BREAKDOWN on a PCG breakdown.
+ */
+LSQ_API lsq_status lsq_pcg_solve(const lsq_matrix* A, const lsq_precond* P, const double* B,
+                         int64_t k, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o,
+                         lsq_info* info, void* stream);
+
+/*
+ * lsq_pcg_adjoint -- gradients through x = argmin ||A x - b|| (not in the paper; it
+ * reuses the paper's preconditioner for the adjoint normal equation).
+ *
+ * Given solutions X (n x k), right-hand sides B (m x k) and G = dL/dX (n x k): solves
+ * A^T A Lambda = G with the same PCG and preconditioner, then
+ *   grad_b    = A Lambda                                   (device double m x k, ldb)
+ *   grad_vals = sum_c (r_c lambda_c^T - (A lambda_c) x_c^T) on A's pattern, r = b - A x
+ *               (device double[nnz] for CSR, [m*ld] for dense)
+ * Either output may be NULL.  Lambda (device double n x k, ldx) is returned when not NULL.
+ */
+LSQ_API lsq_status lsq_pcg_adjoint(const lsq_matrix* A, const lsq_precond* P, const double* X,
+                           const double* B, const double* G, int64_t k, int64_t ldb,
+                           int64_t ldx, double* grad_b, double* grad_vals, double* Lambda,
+                           const lsq_opts* o, lsq_info* info, void* stream);
+
+/* Convert FP64 values to the LSQ_F32X2 pair format (hi = RN(v), lo = RN(v - hi)),
+ * count elements, device to device. */
+LSQ_API lsq_status lsq_split_f64(const double* src, float* dst_pairs, int64_t count, void* stream);
+
+/* Human-readable name of a status code. */
+LSQ_API const char* lsq_status_string(lsq_status s);
+
+/* Message of the last error in this thread (CUDA error text or argument check). */
+LSQ_API const char* lsq_last_error_string(void);
+
+/* Number of kernels this library launched since load (for launch accounting). */
+LSQ_API int64_t lsq_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSQ_H */

@@ -1,0 +1,217 @@
+"""Python face of the C ABI: same call names, torch tensors as device buffers.
+
+Every function here only builds the C argument structs from tensors and calls into
+liblsq.so; all arithmetic of the method runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+DTYPES = {torch.float64: L.LSQ_F64, torch.float32: L.LSQ_F32, torch.bfloat16: L.LSQ_BF16}
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def opts(**kw) -> L.LsqOpts:
+    """lsq_default_opts() with keyword overrides."""
+    o = L.LsqOpts()
+    L.load().lsq_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Matrix:
+    """A in R^{m x n} as device tensors (dense row-major (m, ld) or CSR)."""
+
+    def __init__(self, dense=None, *, row_ptr=None, col_idx=None, vals=None, n=None,
+                 vals_f64=None, f32x2=None):
+        if dense is not None:
+            assert dense.is_cuda and dense.dim() == 2 and dense.stride(1) == 1
+            self.m, self.n = dense.shape
+            self.ld = dense.stride(0)
+            self.vals = dense
+            self.row_ptr = self.col_idx = None
+            self.nnz = self.m * self.n
+            self.dense = True
+        else:
+            assert row_ptr.dtype == torch.int64 and col_idx.dtype == torch.int32
+            self.m = row_ptr.numel() - 1
+            self.n = int(n)
+            self.ld = 0
+            self.vals, self.row_ptr, self.col_idx = vals, row_ptr, col_idx
+            self.nnz = vals.numel()
+            self.dense = False
+        self.dtype = L.LSQ_F32X2 if f32x2 else DTYPES[self.vals.dtype]
+        self.vals_f64 = vals_f64
+        self.c = L.LsqMatrix(self.m, self.n, self.nnz, 1 if self.dense else 0, self.ld,
+                             _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.vals), self.dtype,
+                             _ptr(vals_f64))
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+def _check(code, where):
+    if code != 0:
+        raise L.LsqError(code, where)
+
+
+def lsq_sample_size(n: int, C_factor: float = 4.0) -> int:
+    return int(L.load().lsq_sample_size(int(n), float(C_factor)))
+
+
+def lsq_sample_rows(A: Matrix, o=None, s: int = 0, stream=None):
+    """Alg. 2 steps 1-2 / Alg. 1 -> (idx int32[s], p float64[s], colscale float64[n])."""
+    o = o or opts()
+    s_eff = s if s else lsq_sample_size(A.n, o.sample_factor)
+    dev = A.vals.device
+    idx = torch.empty(s_eff, dtype=torch.int32, device=dev)
+    p = torch.empty(s_eff, dtype=torch.float64, device=dev)
+    d = torch.empty(A.n, dtype=torch.float64, device=dev)
+    s_out = C.c_int64(0)
+    _check(L.load().lsq_sample_rows(A.ref, C.byref(o), s_eff, _ptr(idx), _ptr(p), _ptr(d),
+                                    C.byref(s_out), _stream(stream)), "lsq_sample_rows")
+    return idx, p, d
+
+
+class Precond:
+    """Owns an lsq_precond handle (Sec. 3.3 + Alg. 3)."""
+
+    def __init__(self, handle, n):
+        self.h = C.c_void_p(handle)
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            L.load().lsq_precond_destroy(self.h)
+            self.h = C.c_void_p(None)
+
+    def M(self, stream=None):
+        out = torch.empty(self.n, self.n, dtype=torch.float64, device="cuda")
+        _check(L.load().lsq_precond_get_M(self.h, _ptr(out), _stream(stream)), "lsq_precond_get_M")
+        return out
+
+    def op(self, stream=None):
+        out = torch.empty(self.n, self.n, dtype=torch.float64, device="cuda")
+        _check(L.load().lsq_precond_get_op(self.h, _ptr(out), _stream(stream)), "lsq_precond_get_op")
+        return out
+
+    def apply(self, r, stream=None):
+        r = r.contiguous()
+        k = 1 if r.dim() == 1 else r.shape[0]
+        e = torch.empty_like(r)
+        _check(L.load().lsq_precond_apply(self.h, _ptr(r), _ptr(e), k, _stream(stream)), "lsq_precond_apply")
+        return e
+
+
+def lsq_build_precond(A: Matrix, idx, p, colscale, o=None, stream=None) -> Precond:
+    o = o or opts()
+    h = C.c_void_p()
+    _check(L.load().lsq_build_precond(A.ref, _ptr(idx), _ptr(p), _ptr(colscale), idx.numel(),
+                                      C.byref(o), C.byref(h), _stream(stream)), "lsq_build_precond")
+    return Precond(h.value, A.n)
+
+
+@dataclass
+class Info:
+    iters: np.ndarray
+    outer: np.ndarray
+    relres_rec: np.ndarray
+    relres_true: np.ndarray
+    relres_raw: np.ndarray
+    converged: np.ndarray
+    status: int
+    s: int = 0
+    nnz_M: int = 0
+    n_fixed_diag: int = 0
+    levels: int = 0
+    solve_ms: float = 0.0
+
+
+def _info(k):
+    arrs = dict(iters=np.zeros(k, np.int32), outer=np.zeros(k, np.int32),
+                relres_rec=np.zeros(k), relres_true=np.zeros(k), relres_raw=np.zeros(k),
+                converged=np.zeros(k, np.uint8))
+    ci = L.LsqInfo(k, *(a.ctypes.data for a in arrs.values()))
+    return ci, arrs
+
+
+def _finish_info(ci, arrs, status):
+    return Info(status=status, s=ci.s, nnz_M=ci.nnz_M, n_fixed_diag=ci.n_fixed_diag,
+                levels=ci.levels, solve_ms=ci.solve_ms, **arrs)
+
+
+ACCEPT = (0, 4)  # ok, not converged (reported in info)
+
+
+def lsq_pcg_solve(A: Matrix, P: Precond, B, o=None, X=None, stream=None, raise_on=None):
+    """Alg. 2 step 4 for k right-hand sides (B: (m,) or (k, m) float64) -> (X, Info)."""
+    o = o or opts()
+    B2 = B.reshape(1, -1) if B.dim() == 1 else B
+    assert B2.dtype == torch.float64 and B2.stride(1) == 1
+    k = B2.shape[0]
+    if X is None:
+        X = torch.empty(k, A.n, dtype=torch.float64, device=B.device)
+    ci, arrs = _info(k)
+    code = L.load().lsq_pcg_solve(A.ref, P.h, _ptr(B2), k, B2.stride(0), _ptr(X), X.stride(0),
+                                  C.byref(o), C.byref(ci), _stream(stream))
+    if code not in ACCEPT or (raise_on and code in raise_on):
+        raise L.LsqError(code, "lsq_pcg_solve")
+    return (X.reshape(-1) if B.dim() == 1 else X), _finish_info(ci, arrs, code)
+
+
+def lsq_pcg_adjoint(A: Matrix, P: Precond, X, B, G, o=None, want_grad_vals=True, stream=None):
+    """Adjoint solve -> (grad_b (k, m), grad_vals (like A's values, FP64), Lambda (k, n), Info)."""
+    o = o or opts()
+    X2, B2, G2 = (t.reshape(1, -1) if t.dim() == 1 else t for t in (X, B, G))
+    k = X2.shape[0]
+    gb = torch.empty(k, A.m, dtype=torch.float64, device=X.device)
+    lam = torch.empty(k, A.n, dtype=torch.float64, device=X.device)
+    gv = None
+    if want_grad_vals:
+        gv = torch.zeros(A.m, A.ld, dtype=torch.float64, device=X.device) if A.dense else \
+            torch.zeros(A.nnz, dtype=torch.float64, device=X.device)
+    ci, arrs = _info(k)
+    code = L.load().lsq_pcg_adjoint(A.ref, P.h, _ptr(X2), _ptr(B2), _ptr(G2), k, B2.stride(0),
+                                    X2.stride(0), _ptr(gb), _ptr(gv), _ptr(lam), C.byref(o),
+                                    C.byref(ci), _stream(stream))
+    if code not in ACCEPT:
+        raise L.LsqError(code, "lsq_pcg_adjoint")
+    return gb, gv, lam, _finish_info(ci, arrs, code)
+
+
+def lsq_split_f64(src, stream=None):
+    """FP64 -> interleaved (hi, lo) float pairs (the LSQ_F32X2 storage)."""
+    dst = torch.empty(src.numel() * 2, dtype=torch.float32, device=src.device)
+    _check(L.load().lsq_split_f64(_ptr(src), _ptr(dst), src.numel(), _stream(stream)), "lsq_split_f64")
+    return dst
+
+
+def launches() -> int:
+    return int(L.load().lsq_kernel_launch_count())
+
+
+def solve(A: Matrix, b, o=None, stream=None):
+    """Alg. 2 end to end: sample, build the preconditioner, PCG. Returns (x, Info, extras)."""
+    o = o or opts()
+    idx, p, d = lsq_sample_rows(A, o, stream=stream)
+    P = lsq_build_precond(A, idx, p, d, o, stream=stream)
+    x, info = lsq_pcg_solve(A, P, b, o, stream=stream)
+    return x, info, dict(idx=idx, p=p, colscale=d, P=P)

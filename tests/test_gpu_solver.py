@@ -1,0 +1,176 @@
+"""S5-S9 on the GPU vs the oracle: sampled normal matrix, SGS operator, PCG, adjoint."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from helpers import rel, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(lsq, orc, mat, seed, sweeps=1, dtype="f64", pdt=0, with_f64=False):
+    Mx, keep, seen = to_device(lsq, mat, dtype, with_f64=with_f64)
+    o = lsq.opts(seed=seed, sweeps=sweeps, precond_dtype=pdt)
+    idx, p, d = lsq.lsq_sample_rows(Mx, o)
+    P = lsq.lsq_build_precond(Mx, idx, p, d, o)
+    smp = orc.Sample(seen, seed=seed)
+    Mo = orc.SampledM(smp)
+    return Mx, keep, seen, o, P, smp, Mo
+
+
+@pytest.mark.parametrize("gen", ["gauss", "udv", "tail"])
+def test_sampled_normal_matrix(lsq, orc, gen):
+    mat = {"gauss": lambda: W.gaussian_dense(4096, 128, 1001),
+           "udv": lambda: W.udv_dense(8192, 96, 1e4, 2),
+           "tail": lambda: W.gaussian_dense(1111, 70, 5)}[gen]()
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1001)
+    Mg = P.M().cpu().numpy()
+    Md = Mo.dense()
+    assert np.array_equal(Mg, Mg.T)
+    np.testing.assert_allclose(Mg, Md, rtol=1e-12, atol=1e-13 * np.abs(Md).max())
+
+
+def test_unsampled_column_diagonal(lsq, orc):
+    A = np.random.default_rng(1).standard_normal((400, 6))
+    A[:, 4] = 0.0
+    A[399, 4] = 1e-3                      # almost never drawn with s = 43
+    mat = {"kind": "dense", "A": A}
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 5)
+    Mg = P.M().cpu().numpy()
+    if 399 not in smp.idx:
+        assert Mg[4, 4] == 1.0 and Mo.n_fixed_diag == 1
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+def test_sgs_operator_matches_alg3(lsq, orc, sweeps):
+    mat = W.gaussian_dense(4096, 128, 1001)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1001, sweeps=sweeps)
+    rng = np.random.default_rng(sweeps)
+    R = rng.standard_normal((4, 128))
+    E = P.apply(torch.from_numpy(R).cuda()).cpu().numpy()
+    for c in range(4):
+        ref = orc.sgs_apply(Mo, R[c], sweeps)
+        assert rel(E[c], ref) <= 1e-12
+
+
+def test_sgs_operator_ill_conditioned_and_f32(lsq, orc):
+    mat = W.udv_dense(20000, 256, 1e6, 2)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1002)
+    r = np.random.default_rng(0).standard_normal(256)
+    ref = orc.sgs_apply(Mo, r, 1)
+    e = P.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert rel(e, ref) <= 1e-9
+    P32 = lsq.lsq_build_precond(Mx, *lsq.lsq_sample_rows(Mx, o), lsq.opts(seed=1002, precond_dtype=1))
+    e32 = P32.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert rel(e32, ref) <= 1e-4
+
+
+def _solve_and_compare(lsq, orc, mat, seed, noise, tol=1e-10, iter_slack=2, dtype="f64",
+                       with_f64=False, pdt=0, k=1, **okw):
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, seed, dtype=dtype, pdt=pdt, with_f64=with_f64)
+    for kk, v in okw.items():
+        setattr(o, kk, v)
+    o.tol = tol
+    xs, b = W.rhs_for(seen, k, noise, seed + 7)
+    B = torch.from_numpy(b).cuda()
+    X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    X = X.cpu().numpy()
+    A = seen["A"]
+    kappa = np.linalg.cond(A / smp.d)
+    for c in range(k):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=tol, maxit=o.maxit, max_outer=o.max_outer)
+        x_or = y / smp.d
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert info.relres_true[c] <= tol
+        r = A.T @ (b[c] - A @ X[c])
+        raw = np.linalg.norm(r) / np.linalg.norm(A.T @ b[c])
+        assert abs(raw - info.relres_raw[c]) <= 1e-3 * raw + 1e-15
+        # both solutions satisfy the normal equation to tol: they can differ by
+        # kappa(Â)^2 (tol_gpu + tol_oracle) in the worst direction, and no more
+        assert rel(X[c], x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * tol)
+        if iter_slack is not None:
+            assert abs(int(info.iters[c]) - oi["iters"]) <= iter_slack, (info.iters[c], oi["iters"])
+    return info
+
+
+def test_pcg_config1_gaussian(lsq, orc):
+    # 4096 x 128 Gaussian, b = A x* + 1e-3 noise, one forward + one backward sweep, 1e-10
+    info = _solve_and_compare(lsq, orc, W.gaussian_dense(4096, 128, 1001), 1001, 1e-3)
+    assert info.iters[0] < 40
+
+
+@pytest.mark.parametrize("shape", [(3001, 70), (20000, 256), (9000, 1000)])
+def test_pcg_ragged_and_large_n(lsq, orc, shape):
+    m, n = shape
+    _solve_and_compare(lsq, orc, W.gaussian_dense(m, n, 11), 11, 1e-2)
+
+
+def test_pcg_udv_moderate_condition(lsq, orc):
+    _solve_and_compare(lsq, orc, W.udv_dense(16384, 64, 1e3, 2), 1002, 1e-6, iter_slack=None)
+
+
+def test_pcg_multiple_rhs_and_sweeps(lsq, orc):
+    _solve_and_compare(lsq, orc, W.gaussian_dense(5000, 100, 4), 4, 1e-3, k=3, sweeps=1)
+
+
+def test_pcg_f32_values_with_f64_refinement(lsq, orc):
+    # precision form: FP32 A and operator in the iteration, FP64 residuals/dots/updates
+    info = _solve_and_compare(lsq, orc, W.udv_dense(16384, 128, 1e2, 3), 1002, 1e-6,
+                              dtype="f32", with_f64=True, pdt=1, iter_slack=None, max_outer=30,
+                              inner_tol=1e-4)
+    assert info.outer[0] >= 1
+
+
+def test_pcg_deterministic(lsq, orc):
+    mat = W.gaussian_dense(4096, 128, 1001)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1001)
+    xs, b = W.rhs_for(seen, 1, 1e-3, 3)
+    B = torch.from_numpy(b).cuda()
+    X1, _ = lsq.lsq_pcg_solve(Mx, P, B, o)
+    X2, _ = lsq.lsq_pcg_solve(Mx, P, B, o)
+    assert torch.equal(X1, X2)
+
+
+def test_pcg_zero_rhs_and_maxit(lsq, orc):
+    mat = W.gaussian_dense(2000, 40, 2)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 3)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.zeros(2000, dtype=torch.float64, device="cuda"), o)
+    assert info.iters[0] == 0 and info.converged[0] == 1 and torch.all(X == 0)
+    o.maxit = 3
+    xs, b = W.rhs_for(seen, 1, 1e-3, 3)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
+    assert info.status == 4 and info.iters[0] == 3 and info.converged[0] == 0
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=3, max_outer=o.max_outer)
+    assert rel(X.cpu().numpy(), y / smp.d) <= 1e-10
+
+
+def test_adjoint_matches_oracle(lsq, orc):
+    mat = W.gaussian_dense(3000, 48, 6)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 6)
+    o.tol = 1e-12
+    xs, b = W.rhs_for(seen, 2, 1e-2, 8)
+    B = torch.from_numpy(b).cuda()
+    X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    G = 2 * (X - torch.from_numpy(xs).cuda())
+    gb, gv, lam, ainfo = lsq.lsq_pcg_adjoint(Mx, P, X, B, G, o)
+    Xh, Gh = X.cpu().numpy(), G.cpu().numpy()
+    gA_sum = 0
+    for c in range(2):
+        gbr, gAr, lamr, _ = orc.adjoint(seen, smp, Mo, Xh[c], b[c], Gh[c], tol=1e-12)
+        assert rel(lam[c].cpu().numpy(), lamr) <= 1e-8
+        assert rel(gb[c].cpu().numpy(), gbr) <= 1e-8
+        gA_sum = gA_sum + gAr
+    assert rel(gv.cpu().numpy(), gA_sum) <= 1e-8
+
+
+def test_bad_arguments(lsq):
+    A = torch.randn(100, 8, dtype=torch.float64, device="cuda")
+    Mx = lsq.Matrix(A)
+    idx, p, d = lsq.lsq_sample_rows(Mx)
+    P = lsq.lsq_build_precond(Mx, idx, p, d)
+    with pytest.raises(lsq.L.LsqError) as e:
+        lsq.lsq_pcg_solve(Mx, P, torch.zeros(99, dtype=torch.float64, device="cuda"))
+    assert e.value.code == 1
+    with pytest.raises(lsq.L.LsqError):
+        lsq.lsq_build_precond(Mx, idx, p, d, lsq.opts(sweeps=0))

@@ -37,8 +37,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["f64", "f32"], default="f64",
-                    help="f64: FP64 values; f32: FP32 values + FP64 refinement")
+    ap.add_argument("--mode", choices=["f64", "f32", "f32x2"], default="f32x2",
+                    help="f64: FP64 values and arithmetic; f32: FP32 values + FP64 refinement; "
+                         "f32x2: double-float pairs (FP32 units) + FP64 refinement")
     ap.add_argument("--m", type=int, default=262144)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--kappa", type=float, default=1e6)
@@ -194,20 +195,31 @@ def run_ours(args):
     m, n = mat["A"].shape
     A64 = torch.from_numpy(mat["A"]).cuda()
     bd = torch.from_numpy(b).cuda()
+    M64 = api.Matrix(A64)
     if args.mode == "f64":
-        Mx = api.Matrix(A64)
         es, es_res, es_op, pdt, dtype = 8, 8, 8, 0, "f64"
-    else:
-        A32 = A64.float()
-        Mx = api.Matrix(A32, vals_f64=A64)
+    elif args.mode == "f32":
         es, es_res, es_op, pdt, dtype = 4, 8, 4, 1, "f32+f64"
+    else:
+        es, es_res, es_op, pdt, dtype = 8, 8, 8, 0, "f32x2+f64"
+
+    def solve_matrix(Asrc, Msrc):
+        """The matrix the PCG iteration reads, derived from the FP64 input in-step."""
+        if args.mode == "f64":
+            return Msrc, None
+        if args.mode == "f32":
+            A32 = Asrc.float()
+            return api.Matrix(A32, vals_f64=Asrc), A32
+        pairs = api.lsq_split_f64(Asrc)
+        return api.Matrix(pairs, f32x2=True, vals_f64=Asrc), pairs
     o = api.opts(seed=1002 + rank, tol=args.tol, maxit=args.maxit, precond_dtype=pdt,
                  inner_tol=args.inner_tol, max_outer=50)
     stream = torch.cuda.current_stream()
 
     def step():
-        idx, p, d = api.lsq_sample_rows(Mx, o)
-        P = api.lsq_build_precond(Mx, idx, p, d, o)
+        idx, p, d = api.lsq_sample_rows(M64, o)
+        P = api.lsq_build_precond(M64, idx, p, d, o)
+        Mx, keep = solve_matrix(A64, M64)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -276,12 +288,10 @@ def run_ours(args):
         s0.record(stream)
         dA = hA.to("cuda", non_blocking=True)
         db = hb.to("cuda", non_blocking=True)
-        if args.mode == "f64":
-            Mh = api.Matrix(dA)
-        else:
-            Mh = api.Matrix(dA.float(), vals_f64=dA)
-        idx, p, d = api.lsq_sample_rows(Mh, o)
-        P = api.lsq_build_precond(Mh, idx, p, d, o)
+        Mh64 = api.Matrix(dA)
+        idx, p, d = api.lsq_sample_rows(Mh64, o)
+        P = api.lsq_build_precond(Mh64, idx, p, d, o)
+        Mh, keep = solve_matrix(dA, Mh64)
         xe, _ = api.lsq_pcg_solve(Mh, P, db, o)
         hx.copy_(xe, non_blocking=True)
         s1.record(stream)

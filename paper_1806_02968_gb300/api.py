@@ -43,8 +43,13 @@ class Matrix:
                  vals_f64=None, f32x2=None):
         if dense is not None:
             assert dense.is_cuda and dense.dim() == 2 and dense.stride(1) == 1
-            self.m, self.n = dense.shape
-            self.ld = dense.stride(0)
+            if f32x2:   # (m, 2 n) float32: element j of row i is the pair at columns 2j, 2j+1
+                assert dense.dtype == torch.float32 and dense.shape[1] % 2 == 0
+                self.m, self.n = dense.shape[0], dense.shape[1] // 2
+                self.ld = dense.stride(0) // 2
+            else:
+                self.m, self.n = dense.shape
+                self.ld = dense.stride(0)
             self.vals = dense
             self.row_ptr = self.col_idx = None
             self.nnz = self.m * self.n
@@ -198,8 +203,11 @@ def lsq_pcg_adjoint(A: Matrix, P: Precond, X, B, G, o=None, want_grad_vals=True,
 
 
 def lsq_split_f64(src, stream=None):
-    """FP64 -> interleaved (hi, lo) float pairs (the LSQ_F32X2 storage)."""
-    dst = torch.empty(src.numel() * 2, dtype=torch.float32, device=src.device)
+    """FP64 -> interleaved (hi, lo) float pairs (the LSQ_F32X2 storage); a (m, n) input
+    gives a (m, 2 n) float32 tensor."""
+    src = src.contiguous()
+    shape = (*src.shape[:-1], 2 * src.shape[-1]) if src.dim() > 0 else (2,)
+    dst = torch.empty(shape, dtype=torch.float32, device=src.device)
     _check(L.load().lsq_split_f64(_ptr(src), _ptr(dst), src.numel(), _stream(stream)), "lsq_split_f64")
     return dst
 

@@ -128,8 +128,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
     if (threadIdx.x == 0) {
         int ok = 1;
         unsigned gen = ld_acquire_u32(bar + 1);
-        __threadfence();
-        unsigned arrived = atom_add_release_u32(bar, 1u);
+        unsigned arrived = atom_add_release_u32(bar, 1u);   // release: this CTA's writes
         if (arrived == nblocks - 1) {
             // last to arrive: reset the count, then open the next generation
             atomicExch(bar, 0u);

@@ -11,7 +11,7 @@ const char* last_error();
 
 static int64_t pick_nmax(int dt, int dtr, int64_t n) {
     const int64_t lo = 128;
-    const int64_t hi = (dt == LSQ_F64 || dtr == LSQ_F64) ? 1024 : 2048;
+    const int64_t hi = (dt == LSQ_F32 && dtr == LSQ_F32) ? 2048 : 1024;
     for (int64_t c = lo; c <= hi; c *= 2)
         if (n <= c) return c;
     return 0;
@@ -52,15 +52,19 @@ static lsq_status check_dense_solve(const lsq_matrix* A, const lsq_precond* P, i
         set_error("sparse PCG is not available in this build");
         return LSQ_ERR_UNSUPPORTED;
     }
-    if (A->dtype != LSQ_F64 && A->dtype != LSQ_F32) {
-        set_error("dense PCG supports F64 and F32 values in this build");
+    if (A->dtype == LSQ_BF16) {
+        set_error("dense PCG supports F64, F32 and F32X2 values in this build");
         return LSQ_ERR_UNSUPPORTED;
     }
     const size_t es = elem_size(A->dtype);
     LSQ_CHECK_ARG(aligned16(A->vals), "A->vals must be 16-byte aligned");
     LSQ_CHECK_ARG(((size_t)A->ld * es) % 16 == 0, "A->ld * element size must be a multiple of 16 bytes");
+    LSQ_CHECK_ARG((size_t)A->ld * es * 3 <= (size_t)ring_bytes(2048),
+                  "dense PCG needs 3 * ld * element size <= the staging ring");
     if (A->vals_f64 && A->dtype != LSQ_F64) {
         LSQ_CHECK_ARG(aligned16(A->vals_f64), "A->vals_f64 must be 16-byte aligned");
+        LSQ_CHECK_ARG((size_t)A->ld * 8 * 3 <= (size_t)ring_bytes(2048),
+                      "dense PCG needs 3 * ld * 8 <= the staging ring for the FP64 residual copy");
     }
     *dt = A->dtype;
     *dtr = (A->dtype == LSQ_F64 || A->vals_f64) ? LSQ_F64 : A->dtype;
@@ -110,7 +114,8 @@ static lsq_status solve_columns(const lsq_matrix* A, const lsq_precond* P, const
         a.out_i = wk.out_i; a.out_d = wk.out_d;
         int G = 0;
         lsq_status ls = dt == LSQ_F64 ? launch_pcg_f64(nmax, P->op_dtype, a, o->grid_ctas, st, &G)
-                                      : launch_pcg_f32(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G);
+                      : dt == LSQ_F32 ? launch_pcg_f32(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G)
+                                      : launch_pcg_f32x2(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G);
         if (ls != LSQ_OK) return ls;
         LSQ_CUDA(cudaGetLastError());
         int32_t oi[4];
@@ -270,6 +275,8 @@ extern "C" lsq_status lsq_pcg_adjoint(const lsq_matrix* A, const lsq_precond* P,
     cudaStream_t st = (cudaStream_t)stream;
     if (A->dtype == LSQ_F64)
         return adjoint_dense<LSQ_F64>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
+    if (A->dtype == LSQ_F32X2)
+        return adjoint_dense<LSQ_F32X2>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
     return adjoint_dense<LSQ_F32>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
 }
 

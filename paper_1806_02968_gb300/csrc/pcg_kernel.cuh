@@ -14,6 +14,8 @@
 //   B3 after z = P g (partials of g^T z).
 #pragma once
 #include "common.cuh"
+#include "tma.cuh"
+#include "dfloat.cuh"
 
 namespace lsq {
 
@@ -43,101 +45,433 @@ struct PcgArgs {
     double* out_d;         // relres_rec, relres_true, relres_raw
 };
 
-// Storage/compute traits of a value dtype for the vectorised row pass.
-template <int DT> struct RowT;
-template <> struct RowT<LSQ_F64> {
-    typedef double C;  // compute type
-    static constexpr int VEC = 2;
-    static __device__ __forceinline__ void load(const void* base, int64_t e, C (&a)[VEC]) {
-        double2 v = __ldg(reinterpret_cast<const double2*>(reinterpret_cast<const double*>(base) + e));
-        a[0] = v.x; a[1] = v.y;
-    }
-};
-template <> struct RowT<LSQ_F32> {
-    typedef float C;
-    static constexpr int VEC = 4;
-    static __device__ __forceinline__ void load(const void* base, int64_t e, C (&a)[VEC]) {
-        float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(base) + e));
-        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
-    }
-};
+__device__ __forceinline__ int64_t imin64(int64_t x, int64_t y) { return x < y ? x : y; }
 
-template <typename T>
-__device__ __forceinline__ T fma_t(T a, T b, T c) { return fma(a, b, c); }
+// Two-row warp reduction (pair_reduce2 below): lanes 0-15 end with sum(a), lanes 16-31
+// with sum(b) (one exchange splits the rows, four butterfly steps finish each half), then
+// both sums are broadcast.
+__device__ __forceinline__ double shfl_d(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_f(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ f2 shfl_f2(f2 v, int o) { return df_shfl_xor(v, o); }
+__device__ __forceinline__ double bcast_d(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ float bcast_f(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ f2 bcast_f2(f2 v, int l) {
+    return f2{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
+}
+template <typename T, typename Add>
+__device__ __forceinline__ void pair_reduce2(T& a, T& b, int lane, Add add, T (*xo)(T, int), T (*bc)(T, int)) {
+    T send = (lane < 16) ? b : a;
+    T mine = (lane < 16) ? a : b;
+    add(mine, xo(send, 16));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) add(mine, xo(mine, o));
+    a = bc(mine, 0);
+    b = bc(mine, 16);
+}
 
-// Fused row pass over rows [r0, r1):
-//   MATVEC: q_i = â_i . p̃      RHS: q_i = b_i      RESID: q_i = b_i - â_i . ỹ
-// with p̃ / ỹ = D^{-1} (vector) already in s_v (padded with zeros to NMAX).  Each warp
-// accumulates sum_i q_i a_i in registers; the CTA partial (sum over warps in order) is
-// written to part_w[cta][0..n) and sum_i q_i^2 to part_s[cta][0].
-template <int DT, int NMAX>
-__device__ __forceinline__ void row_pass(const PcgArgs& a, const void* vals, int mode,
-                                         const double* s_v, double* s_red, double* s_scal,
-                                         int64_t r0, int64_t r1) {
-    typedef typename RowT<DT>::C C;
-    constexpr int VEC = RowT<DT>::VEC;
-    constexpr int NCH = NMAX / (32 * VEC);
-    static_assert(NCH >= 1, "NMAX too small for this dtype");
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int64_t n = a.n;
-    C acc[NCH][VEC];
+// Per-dtype arithmetic of the fused row pass.  A lane owns VEC consecutive elements of
+// each 32*VEC-wide chunk of a row (16-byte shared-memory reads); NCH chunks cover NMAX.
+// A warp handles one row, or two rows at once (TWO) whose dot products share one warp
+// reduction.  Elements beyond n (row padding) are masked to zero.
+//   LSQ_F64   : FP64 products and sums.
+//   LSQ_F32   : FP32 products, FP32 row dots and column accumulators; sum of q_i^2 in
+//               double-float (no FP64 instruction per row).
+//   LSQ_F32X2 : values stored as float pairs (hi, lo); products and sums in double-float
+//               (about 48 bits) on the FP32 units.
+template <int DT, int NMAX> struct RowOps;
+
+template <int NMAX> struct RowOps<LSQ_F64, NMAX> {
+    static constexpr int ES = 8, VEC = 2, NCH = NMAX / (32 * VEC);
+    typedef double VT;   // staged vector element
+    typedef double RT;   // cross-warp reduction element
+    struct Acc { double v[NCH][VEC]; };
+    struct Q { double s; };
+    static __device__ __forceinline__ void zero(Acc& a, Q& q) {
 #pragma unroll
-    for (int c = 0; c < NCH; ++c)
+        for (int c = 0; c < NCH; ++c) { a.v[c][0] = 0.0; a.v[c][1] = 0.0; }
+        q.s = 0.0;
+    }
+    static __device__ __forceinline__ VT stage(double x) { return x; }
+    template <int MODE, bool TWO>
+    static __device__ __forceinline__ void row(const char* rp0, const char* rp1, bool has1,
+                                               const VT* sv, int lane, int64_t n, double b0,
+                                               double b1, Acc& A, Q& Qa) {
+        const double* r0 = reinterpret_cast<const double*>(rp0);
+        const double* r1 = reinterpret_cast<const double*>(rp1);
+        double q0, q1 = 0.0;
+        if (MODE == PASS_RHS) {
+            q0 = b0; q1 = b1;
+        } else {
+            double d0[4] = {0.0, 0.0, 0.0, 0.0}, d1[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[c][v] = C(0);
-    double qq = 0.0;
-    for (int64_t i = r0 + wid; i < r1; i += nwarps) {
-        const int64_t rowoff = i * a.ld;
-        C av[NCH][VEC];
+            for (int c = 0; c < NCH; ++c) {
+                const int col = c * 32 * VEC + lane * VEC;
+                if (col < n) {
+                    const double2 sx = *reinterpret_cast<const double2*>(sv + col);
+                    const bool in1 = col + 1 < n;
+                    double2 v = *reinterpret_cast<const double2*>(r0 + col);
+                    d0[(2 * c) & 3] = fma(v.x, sx.x, d0[(2 * c) & 3]);
+                    d0[(2 * c + 1) & 3] = fma(in1 ? v.y : 0.0, sx.y, d0[(2 * c + 1) & 3]);
+                    if (TWO) {
+                        double2 w = *reinterpret_cast<const double2*>(r1 + col);
+                        d1[(2 * c) & 3] = fma(w.x, sx.x, d1[(2 * c) & 3]);
+                        d1[(2 * c + 1) & 3] = fma(in1 ? w.y : 0.0, sx.y, d1[(2 * c + 1) & 3]);
+                    }
+                }
+            }
+            double d0s = (d0[0] + d0[1]) + (d0[2] + d0[3]), d1s = (d1[0] + d1[1]) + (d1[2] + d1[3]);
+            if (TWO) pair_reduce2<double>(d0s, d1s, lane, [](double& x, double y) { x += y; }, shfl_d, bcast_d);
+            else d0s = warp_sum(d0s);
+            q0 = (MODE == PASS_MATVEC) ? d0s : b0 - d0s;
+            q1 = (MODE == PASS_MATVEC) ? d1s : b1 - d1s;
+        }
+        if (!has1) q1 = 0.0;
+        if (lane == 0) { Qa.s = fma(q0, q0, Qa.s); if (TWO) Qa.s = fma(q1, q1, Qa.s); }
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             const int col = c * 32 * VEC + lane * VEC;
             if (col < n) {
-                RowT<DT>::load(vals, rowoff + col, av[c]);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v)
-                    if (col + v >= n) av[c][v] = C(0);
-            } else {
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) av[c][v] = C(0);
+                const bool in1 = col + 1 < n;
+                double2 v = *reinterpret_cast<const double2*>(r0 + col);
+                A.v[c][0] = fma(q0, v.x, A.v[c][0]);
+                A.v[c][1] = fma(q0, in1 ? v.y : 0.0, A.v[c][1]);
+                if (TWO) {
+                    double2 w = *reinterpret_cast<const double2*>(r1 + col);
+                    A.v[c][0] = fma(q1, w.x, A.v[c][0]);
+                    A.v[c][1] = fma(q1, in1 ? w.y : 0.0, A.v[c][1]);
+                }
             }
         }
-        double q;
-        if (mode == PASS_RHS) {
-            q = a.b[i];
-        } else {
-            C dot = C(0);
+    }
+    static __device__ __forceinline__ void store(const Acc& A, RT* dst, int lane) {
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                const int col = c * 32 * VEC + lane * VEC;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) dot = fma_t(av[c][v], (C)s_v[col + v], dot);
-            }
-            dot = warp_sum(dot);
-            q = (mode == PASS_MATVEC) ? (double)dot : a.b[i] - (double)dot;
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            *reinterpret_cast<double2*>(dst + col) = make_double2(A.v[c][0], A.v[c][1]);
         }
-        qq = fma(q, q, qq);
-        const C qc = (C)q;
+    }
+    static __device__ __forceinline__ void red_add(RT& acc, RT v) { acc += v; }
+    static __device__ __forceinline__ RT red_zero() { return 0.0; }
+    static __device__ __forceinline__ double red_out(RT v) { return v; }
+    static __device__ __forceinline__ double q_out(const Q& q) { return q.s; }
+};
+
+template <int NMAX> struct RowOps<LSQ_F32, NMAX> {
+    static constexpr int ES = 4, VEC = 4, NCH = NMAX / (32 * VEC);
+    typedef float VT;
+    typedef float RT;
+    struct Acc { float v[NCH][VEC]; };
+    struct Q { f2 s; };
+    static __device__ __forceinline__ void zero(Acc& a, Q& q) {
 #pragma unroll
         for (int c = 0; c < NCH; ++c)
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] = fma_t(qc, av[c][v], acc[c][v]);
+            for (int v = 0; v < VEC; ++v) a.v[c][v] = 0.f;
+        q.s = f2{0.f, 0.f};
     }
-    // cross-warp reduction in a fixed order
-    double* mine = s_red + (int64_t)wid * NMAX;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        const int col = c * 32 * VEC + lane * VEC;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) mine[col + v] = (double)acc[c][v];
+    static __device__ __forceinline__ VT stage(double x) { return (float)x; }
+    static __device__ __forceinline__ float4 masked(float4 v, int col, int64_t n) {
+        if (col + 4 <= n) return v;
+        return make_float4(v.x, col + 1 < n ? v.y : 0.f, col + 2 < n ? v.z : 0.f, col + 3 < n ? v.w : 0.f);
     }
-    if (lane == 0) s_scal[wid] = qq;  // qq is identical in all lanes; keep one copy
+    template <int MODE, bool TWO>
+    static __device__ __forceinline__ void row(const char* rp0, const char* rp1, bool has1,
+                                               const VT* sv, int lane, int64_t n, double b0,
+                                               double b1, Acc& A, Q& Qa) {
+        const float* r0 = reinterpret_cast<const float*>(rp0);
+        const float* r1 = reinterpret_cast<const float*>(rp1);
+        float q0, q1 = 0.f;
+        if (MODE == PASS_RHS) {
+            q0 = (float)b0; q1 = (float)b1;
+        } else {
+            float4 d0 = make_float4(0.f, 0.f, 0.f, 0.f), d1 = d0;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int col = c * 32 * VEC + lane * VEC;
+                if (col < n) {
+                    const float4 sx = *reinterpret_cast<const float4*>(sv + col);
+                    const float4 v = masked(*reinterpret_cast<const float4*>(r0 + col), col, n);
+                    d0.x = fmaf(v.x, sx.x, d0.x); d0.y = fmaf(v.y, sx.y, d0.y);
+                    d0.z = fmaf(v.z, sx.z, d0.z); d0.w = fmaf(v.w, sx.w, d0.w);
+                    if (TWO) {
+                        const float4 w = masked(*reinterpret_cast<const float4*>(r1 + col), col, n);
+                        d1.x = fmaf(w.x, sx.x, d1.x); d1.y = fmaf(w.y, sx.y, d1.y);
+                        d1.z = fmaf(w.z, sx.z, d1.z); d1.w = fmaf(w.w, sx.w, d1.w);
+                    }
+                }
+            }
+            float d0s = (d0.x + d0.y) + (d0.z + d0.w), d1s = (d1.x + d1.y) + (d1.z + d1.w);
+            if (TWO) pair_reduce2<float>(d0s, d1s, lane, [](float& x, float y) { x += y; }, shfl_f, bcast_f);
+            else d0s = warp_sum(d0s);
+            if (MODE == PASS_MATVEC) { q0 = d0s; q1 = d1s; }
+            else { q0 = (float)(b0 - (double)d0s); q1 = (float)(b1 - (double)d1s); }
+        }
+        if (!has1) q1 = 0.f;
+        df_add_sq(Qa.s, q0);
+        if (TWO) df_add_sq(Qa.s, q1);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            if (col < n) {
+                const float4 v = masked(*reinterpret_cast<const float4*>(r0 + col), col, n);
+                A.v[c][0] = fmaf(q0, v.x, A.v[c][0]); A.v[c][1] = fmaf(q0, v.y, A.v[c][1]);
+                A.v[c][2] = fmaf(q0, v.z, A.v[c][2]); A.v[c][3] = fmaf(q0, v.w, A.v[c][3]);
+                if (TWO) {
+                    const float4 w = masked(*reinterpret_cast<const float4*>(r1 + col), col, n);
+                    A.v[c][0] = fmaf(q1, w.x, A.v[c][0]); A.v[c][1] = fmaf(q1, w.y, A.v[c][1]);
+                    A.v[c][2] = fmaf(q1, w.z, A.v[c][2]); A.v[c][3] = fmaf(q1, w.w, A.v[c][3]);
+                }
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(const Acc& A, RT* dst, int lane) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            *reinterpret_cast<float4*>(dst + col) = make_float4(A.v[c][0], A.v[c][1], A.v[c][2], A.v[c][3]);
+        }
+    }
+    static __device__ __forceinline__ void red_add(RT& acc, RT v) { acc += v; }
+    static __device__ __forceinline__ RT red_zero() { return 0.f; }
+    static __device__ __forceinline__ double red_out(RT v) { return (double)v; }
+    static __device__ __forceinline__ double q_out(const Q& q) { return df_to_double(q.s); }
+};
+
+template <int NMAX> struct RowOps<LSQ_F32X2, NMAX> {
+    static constexpr int ES = 8, VEC = 2, NCH = NMAX / (32 * VEC);
+    typedef f2 VT;
+    typedef f2 RT;
+    struct Acc { f2 v[NCH][VEC]; };
+    struct Q { f2 s; };
+    static __device__ __forceinline__ void zero(Acc& a, Q& q) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { a.v[c][0] = f2{0.f, 0.f}; a.v[c][1] = f2{0.f, 0.f}; }
+        q.s = f2{0.f, 0.f};
+    }
+    static __device__ __forceinline__ VT stage(double x) { return df_from_double(x); }
+    template <int MODE, bool TWO>
+    static __device__ __forceinline__ void row(const char* rp0, const char* rp1, bool has1,
+                                               const VT* sv, int lane, int64_t n, double b0,
+                                               double b1, Acc& A, Q& Qa) {
+        const float* r0 = reinterpret_cast<const float*>(rp0);
+        const float* r1 = reinterpret_cast<const float*>(rp1);
+        f2 q0, q1{0.f, 0.f};
+        if (MODE == PASS_RHS) {
+            q0 = df_from_double(b0); q1 = df_from_double(b1);
+        } else {
+            f2 d0[4], d1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { d0[k] = f2{0.f, 0.f}; d1[k] = f2{0.f, 0.f}; }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int col = c * 32 * VEC + lane * VEC;
+                if (col < n) {
+                    const float4 sx = *reinterpret_cast<const float4*>(sv + col);   // two pairs
+                    const bool in1 = col + 1 < n;
+                    const float4 v = *reinterpret_cast<const float4*>(r0 + 2 * col);  // hi0 lo0 hi1 lo1
+                    df_fma(d0[(2 * c) & 3], f2{v.x, v.y}, f2{sx.x, sx.y});
+                    if (in1) df_fma(d0[(2 * c + 1) & 3], f2{v.z, v.w}, f2{sx.z, sx.w});
+                    if (TWO) {
+                        const float4 w = *reinterpret_cast<const float4*>(r1 + 2 * col);
+                        df_fma(d1[(2 * c) & 3], f2{w.x, w.y}, f2{sx.x, sx.y});
+                        if (in1) df_fma(d1[(2 * c + 1) & 3], f2{w.z, w.w}, f2{sx.z, sx.w});
+                    }
+                }
+            }
+            df_add(d0[0], d0[1]); df_add(d0[2], d0[3]); df_add(d0[0], d0[2]);
+            df_add(d1[0], d1[1]); df_add(d1[2], d1[3]); df_add(d1[0], d1[2]);
+            f2 d0a = d0[0], d1a = d1[0];
+            if (TWO) pair_reduce2<f2>(d0a, d1a, lane, [](f2& x, f2 y) { df_add(x, y); }, shfl_f2, bcast_f2);
+            else d0a = df_warp_sum(d0a);
+            if (MODE == PASS_MATVEC) { q0 = d0a; q1 = d1a; }
+            else { q0 = df_from_double(b0 - df_to_double(d0a)); q1 = df_from_double(b1 - df_to_double(d1a)); }
+        }
+        if (!has1) q1 = f2{0.f, 0.f};
+        df_fma(Qa.s, q0, q0);
+        if (TWO) df_fma(Qa.s, q1, q1);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            if (col < n) {
+                const bool in1 = col + 1 < n;
+                const float4 v = *reinterpret_cast<const float4*>(r0 + 2 * col);
+                df_fma(A.v[c][0], q0, f2{v.x, v.y});
+                if (in1) df_fma(A.v[c][1], q0, f2{v.z, v.w});
+                if (TWO) {
+                    const float4 w = *reinterpret_cast<const float4*>(r1 + 2 * col);
+                    df_fma(A.v[c][0], q1, f2{w.x, w.y});
+                    if (in1) df_fma(A.v[c][1], q1, f2{w.z, w.w});
+                }
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(const Acc& A, RT* dst, int lane) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            *reinterpret_cast<float4*>(dst + col) =
+                make_float4(A.v[c][0].hi, A.v[c][0].lo, A.v[c][1].hi, A.v[c][1].lo);
+        }
+    }
+    static __device__ __forceinline__ void red_add(RT& acc, RT v) { df_add(acc, v); }
+    static __device__ __forceinline__ RT red_zero() { return f2{0.f, 0.f}; }
+    static __device__ __forceinline__ double red_out(RT v) { return df_to_double(v); }
+    static __device__ __forceinline__ double q_out(const Q& q) { return df_to_double(q.s); }
+};
+
+// Shared-memory staging ring for the rows of A; one mbarrier per slot.  The rest of the
+// 208 KiB budget holds four n-vectors (p, the staged vector in FP64 and in the compute
+// type, and 1/d).
+constexpr int RING_SLOTS = 8;
+constexpr int PCG_VEC_ARRAYS = 4;  // s_p, s_v, s_vc, s_invd (NMAX doubles each)
+__host__ __device__ constexpr int ring_bytes(int nmax) {
+    return ((208 * 1024 - PCG_VEC_ARRAYS * nmax * 8) / (16 * 1024)) * 16 * 1024;
+}
+// Dynamic shared memory of k_pcg_dense: the ring followed by the n-vectors.  The kernel's
+// layout and the launcher both use this one definition.
+__host__ __device__ constexpr size_t pcg_smem_bytes(int nmax) {
+    return (size_t)ring_bytes(nmax) + (size_t)PCG_VEC_ARRAYS * nmax * sizeof(double);
+}
+struct Ring {
+    char* buf;
+    uint64_t* bars;
+    uint32_t phase;       // bit s: parity of the next wait on slot s (same in every thread)
+    int bytes;
+    const char* pre_src;  // stages already in flight for a pass starting at pre_src
+    uint32_t pre_stage;
+    int pre_count;
+};
+// Stage geometry of a pass: rows per warp (2 when four stages of 2 rows per warp fit),
+// rows per stage R, slots in the ring (>= 3 unless a row is very long).
+struct Geo {
+    int rpw, R, slots;
+    uint32_t row_bytes, stage_bytes;
+};
+__device__ __forceinline__ Geo geometry(int64_t ld, int es, int nwarps, int rbytes) {
+    Geo g;
+    g.row_bytes = (uint32_t)(ld * es);
+    if ((int64_t)4 * 2 * nwarps * g.row_bytes <= rbytes) {
+        g.rpw = 2;
+        g.R = 2 * nwarps;
+    } else {
+        g.rpw = 1;
+        g.R = (int)(rbytes / (3 * (int64_t)g.row_bytes));
+        if (g.R > nwarps) g.R = nwarps;
+        if (g.R < 1) g.R = 1;
+    }
+    g.stage_bytes = (uint32_t)g.R * g.row_bytes;
+    g.slots = rbytes / (int)g.stage_bytes;
+    if (g.slots > RING_SLOTS) g.slots = RING_SLOTS;
+    if (g.slots < 1) g.slots = 1;
+    return g;
+}
+// thread 0: start the bulk copy of `bytes` at src into slot `slot`
+__device__ __forceinline__ void ring_issue(Ring& ring, int slot, const Geo& g, const char* src, uint32_t bytes) {
+    mbar_expect_tx(&ring.bars[slot], bytes);
+    bulk_g2s(ring.buf + slot * g.stage_bytes, src, bytes, &ring.bars[slot]);
+}
+// all threads: wait for slot `slot`, flip its phase bit
+__device__ __forceinline__ bool ring_wait(Ring& ring, int slot) {
+    const bool ok = mbar_wait(&ring.bars[slot], (ring.phase >> slot) & 1u);
+    ring.phase ^= (1u << slot);
+    return ok;
+}
+// all threads: consume stages issued ahead that no pass will use, so the ring is idle
+__device__ __forceinline__ void ring_drain(Ring& ring) {
+    for (int i = 0; i < ring.pre_count; ++i) ring_wait(ring, i);
+    ring.pre_count = 0;
+    __syncthreads();
+}
+// all threads (uniform arguments): issue the first stages of a pass over `nrows` rows
+// starting at src, ahead of time.  The ring must be idle.
+__device__ __forceinline__ void ring_prefetch(Ring& ring, const char* src, const Geo& g, int64_t nrows) {
+    const int nst = (int)((nrows + g.R - 1) / g.R);
+    const int cnt = nst < g.slots ? nst : g.slots;
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        for (int i = 0; i < cnt; ++i)
+            ring_issue(ring, i, g, src + (int64_t)i * g.stage_bytes,
+                       (uint32_t)imin64(g.R, nrows - (int64_t)i * g.R) * g.row_bytes);
+    }
+    ring.pre_src = src;
+    ring.pre_stage = g.stage_bytes;
+    ring.pre_count = cnt;
+}
+
+// Fused row pass over the CTA's rows [r0, r1), streamed HBM -> shared memory with 1D bulk
+// copies (the row block is one contiguous byte range):
+//   MATVEC: q_i = â_i . p̃      RHS: q_i = b_i      RESID: q_i = b_i - â_i . ỹ
+// with p̃ / ỹ = D^{-1} (vector) in s_v (zero beyond n).  Each warp accumulates
+// sum_i q_i a_i in registers; the CTA partial (warps summed in order) goes to
+// part_w[cta][0..n) and sum_i q_i^2 to part_s[cta][0].  Stages already in flight for this
+// pass (ring_prefetch) are used; stages in flight for another pass are drained first.
+// Returns false if a stage never arrived (bounded wait; the error word is set).
+template <int DT, int NMAX, int MODE, int RPW>
+__device__ __forceinline__ bool row_pass_rpw(const PcgArgs& a, const void* vals, const double* s_v,
+                                             void* s_vc_raw, double* s_scal, int64_t r0, int64_t r1,
+                                             Ring& ring, const Geo g) {
+    typedef RowOps<DT, NMAX> Ops;
+    typedef typename Ops::VT VT;
+    typedef typename Ops::RT RT;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t n = a.n;
+    VT* s_vc = reinterpret_cast<VT*>(s_vc_raw);
+    for (int j = threadIdx.x; j < NMAX; j += blockDim.x) s_vc[j] = Ops::stage(s_v[j]);
+    const int nrows = (int)(r1 - r0);
+    const int nst = (nrows + g.R - 1) / g.R;
+    const char* src = reinterpret_cast<const char*>(vals) + r0 * (int64_t)g.row_bytes;
+    int have = 0;
+    if (ring.pre_count > 0) {
+        if (ring.pre_src == src && ring.pre_stage == g.stage_bytes) have = ring.pre_count;
+        else ring_drain(ring);
+    }
+    ring.pre_count = 0;
+    __syncthreads();   // s_vc ready; previous users of the ring are done
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        for (int i = have; i < nst && i < g.slots; ++i)
+            ring_issue(ring, i, g, src + (int64_t)i * g.stage_bytes,
+                       (uint32_t)min(g.R, nrows - i * g.R) * g.row_bytes);
+    }
+    typename Ops::Acc acc;
+    typename Ops::Q qacc;
+    Ops::zero(acc, qacc);
+    bool ok = true;
+    int slot = 0;
+    for (int i = 0; i < nst; ++i) {
+        if (!ring_wait(ring, slot)) ok = false;
+        const int rows_here = min(g.R, nrows - i * g.R);
+        const int lr = wid * RPW;    // first local row of this warp
+        if (ok && lr < rows_here) {
+            const char* base = ring.buf + slot * g.stage_bytes;
+            const int64_t gi = r0 + (int64_t)i * g.R + lr;
+            const bool has1 = (RPW == 2) && (lr + 1 < rows_here);
+            const double b0 = (MODE == PASS_MATVEC) ? 0.0 : a.b[gi];
+            const double b1 = (MODE == PASS_MATVEC || !has1) ? 0.0 : a.b[gi + 1];
+            const char* rp0 = base + lr * g.row_bytes;
+            const char* rp1 = has1 ? rp0 + g.row_bytes : rp0;
+            Ops::template row<MODE, RPW == 2>(rp0, rp1, has1, s_vc, lane, n, b0, b1, acc, qacc);
+        }
+        __syncthreads();   // every warp is done with this slot
+        if (threadIdx.x == 0 && i + g.slots < nst) {
+            fence_proxy_async_smem();
+            const int k = i + g.slots;
+            ring_issue(ring, slot, g, src + (int64_t)k * g.stage_bytes,
+                       (uint32_t)min(g.R, nrows - k * g.R) * g.row_bytes);
+        }
+        slot = (slot + 1 == g.slots) ? 0 : slot + 1;
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    // cross-warp reduction in a fixed order (the drained ring holds the per-warp vectors)
+    RT* s_red = reinterpret_cast<RT*>(ring.buf);
+    Ops::store(acc, s_red + (int64_t)wid * NMAX, lane);
+    if (lane == 0) s_scal[wid] = Ops::q_out(qacc);
     __syncthreads();
     double* pw = a.part_w + (int64_t)blockIdx.x * n;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        double sacc = 0.0;
-        for (int w = 0; w < nwarps; ++w) sacc += s_red[(int64_t)w * NMAX + j];
-        pw[j] = sacc;
+        RT sacc = Ops::red_zero();
+        for (int w = 0; w < nwarps; ++w) Ops::red_add(sacc, s_red[(int64_t)w * NMAX + j]);
+        pw[j] = Ops::red_out(sacc);
     }
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -145,29 +479,47 @@ __device__ __forceinline__ void row_pass(const PcgArgs& a, const void* vals, int
         a.part_s[(int64_t)blockIdx.x * PART_S + 0] = t;
     }
     __syncthreads();
+    return ok;
 }
 
-// sum_g part_s[g][slot] over all CTAs, same order in every CTA; result broadcast.
-__device__ __forceinline__ double grid_scalar(const PcgArgs& a, int slot, double* s_scal) {
+template <int DT, int NMAX, int MODE>
+__device__ __forceinline__ bool row_pass(const PcgArgs& a, const void* vals, const double* s_v,
+                                         void* s_vc_raw, double* s_scal, int64_t r0, int64_t r1,
+                                         Ring& ring) {
+    const Geo g = geometry(a.ld, RowOps<DT, NMAX>::ES, blockDim.x >> 5, ring.bytes);
+    if (g.rpw == 2) return row_pass_rpw<DT, NMAX, MODE, 2>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
+    return row_pass_rpw<DT, NMAX, MODE, 1>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
+}
+
+// sum_g part_s[g][slot] over all CTAs, computed by the calling warp (every warp of every
+// CTA sums in the same order, so all agree bit for bit); no block barrier.
+__device__ __forceinline__ double warp_grid_scalar(const PcgArgs& a, int slot) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        double t = 0.0;
-        for (int g = lane; g < (int)gridDim.x; g += 32) t += a.part_s[(int64_t)g * PART_S + slot];
-        t = warp_sum(t);
-        if (lane == 0) s_scal[31] = t;
+    double t = 0.0;
+    for (int g = lane; g < (int)gridDim.x; g += 32) t += a.part_s[(int64_t)g * PART_S + slot];
+    return warp_sum(t);
+}
+
+// Writes the CTA partials pa, pb (one per warp, in s_scal) to part_s[cta][slot_a/slot_b].
+__device__ __forceinline__ void cta_partials(const PcgArgs& a, double pa, double pb, int slot_a,
+                                             int slot_b, double* s_scal) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 0) { s_scal[wid] = pa; s_scal[32 + wid] = pb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < nwarps; ++w) { ta += s_scal[w]; tb += s_scal[32 + w]; }
+        a.part_s[(int64_t)blockIdx.x * PART_S + slot_a] = ta;
+        a.part_s[(int64_t)blockIdx.x * PART_S + slot_b] = tb;
     }
     __syncthreads();
-    double r = s_scal[31];
-    __syncthreads();
-    return r;
 }
 
-// w_j = inv_d_j sum_g part_w[g][j] for the owned columns, handed (on lane 0 of the warp
-// that reduced it) to `fn(j, w_j)`, which returns this column's contributions to two CTA
-// partials stored in part_s[cta][slot_a] and part_s[cta][slot_b].
+// w_j = (1/d_j) sum_g part_w[g][j] for the owned columns (one warp per column), handed on
+// lane 0 to `fn(j, w_j)`, which returns this column's contributions to two CTA partials.
 template <typename F>
 __device__ __forceinline__ void slice_reduce(const PcgArgs& a, int64_t c0, int64_t c1, int slot_a,
-                                             int slot_b, double* s_scal, F fn) {
+                                             int slot_b, double* s_scal, const double* s_invd, F fn) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     double pa = 0.0, pb = 0.0;
     for (int64_t j = c0 + wid; j < c1; j += nwarps) {
@@ -175,20 +527,12 @@ __device__ __forceinline__ void slice_reduce(const PcgArgs& a, int64_t c0, int64
         for (int g = lane; g < (int)gridDim.x; g += 32) t += a.part_w[(int64_t)g * a.n + j];
         t = warp_sum(t);
         if (lane == 0) {
-            double2 r = fn(j, t * a.inv_d[j]);
+            double2 r = fn(j, t * s_invd[j]);
             pa += r.x;
             pb += r.y;
         }
     }
-    if (lane == 0) { s_scal[wid] = pa; s_scal[16 + wid] = pb; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tb = 0.0;
-        for (int w = 0; w < nwarps; ++w) { ta += s_scal[w]; tb += s_scal[16 + w]; }
-        a.part_s[(int64_t)blockIdx.x * PART_S + slot_a] = ta;
-        a.part_s[(int64_t)blockIdx.x * PART_S + slot_b] = tb;
-    }
-    __syncthreads();
+    cta_partials(a, pa, pb, slot_a, slot_b, s_scal);
 }
 
 // z_j = sum_k op_jk g_k for the owned rows (g staged in s_v); partial g^T z -> slot 2.
@@ -200,36 +544,57 @@ __device__ __forceinline__ void op_rows(const PcgArgs& a, int64_t c0, int64_t c1
     double part = 0.0;
     for (int64_t j = c0 + wid; j < c1; j += nwarps) {
         const OPT* row = op + j * a.n;
-        OPT t = OPT(0);
-        for (int64_t k = lane; k < a.n; k += 32) t = fma(row[k], (OPT)s_v[k], t);
-        double zj = (double)warp_sum(t);
-        if (lane == 0) a.z[j] = zj;
-        part = fma(s_v[j], zj, part);
+        OPT t0 = OPT(0), t1 = OPT(0);
+        int64_t k = lane;
+        for (; k + 32 < a.n; k += 64) {
+            t0 = fma(row[k], (OPT)s_v[k], t0);
+            t1 = fma(row[k + 32], (OPT)s_v[k + 32], t1);
+        }
+        if (k < a.n) t0 = fma(row[k], (OPT)s_v[k], t0);
+        double zj = (double)warp_sum(t0 + t1);
+        if (lane == 0) {
+            a.z[j] = zj;
+            part = fma(s_v[j], zj, part);
+        }
     }
-    if (lane == 0) s_scal[wid] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < nwarps; ++w) t += s_scal[w];
-        a.part_s[(int64_t)blockIdx.x * PART_S + 2] = t;
-    }
-    __syncthreads();
+    cta_partials(a, part, 0.0, 2, 7, s_scal);
 }
 
 template <int DT, int DTR, int NMAX, typename OPT>
-__global__ void __launch_bounds__(256, 1) k_pcg_dense(PcgArgs a) {
-    extern __shared__ double smem[];
-    __shared__ double s_scal[32];
+__global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
+    extern __shared__ __align__(128) char smem_raw[];
+    __shared__ double s_scal[64];
+    __shared__ __align__(8) uint64_t s_bars[RING_SLOTS];
     const int64_t n = a.n;
     const int nwarps = blockDim.x >> 5;
-    double* s_p = smem;              // NMAX: search direction p (replicated)
+    const int lane = threadIdx.x & 31;
+    const int RB = ring_bytes(NMAX);
+    Ring ring{smem_raw, s_bars, 0u, RB, nullptr, 0u, 0};
+    double* s_p = reinterpret_cast<double*>(smem_raw + RB);  // NMAX: p (replicated)
     double* s_v = s_p + NMAX;        // NMAX: D^{-1} x vector for the row pass, or g
-    double* s_red = s_v + NMAX;      // nwarps x NMAX
+    double* s_vc = s_v + NMAX;       // NMAX: s_v in the compute type of the row pass
+    double* s_invd = s_vc + NMAX;    // NMAX: 1 / d_j
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < RING_SLOTS; ++i) mbar_init(&s_bars[i], 1);
+        fence_mbar_init();
+    }
+    for (int64_t j = threadIdx.x; j < NMAX; j += blockDim.x) {
+        s_p[j] = 0.0; s_v[j] = 0.0;
+        s_invd[j] = j < n ? a.inv_d[j] : 0.0;
+    }
+    __syncthreads();
     const unsigned G = gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * a.m / G, r1 = (int64_t)(blockIdx.x + 1) * a.m / G;
     const int64_t c0 = (int64_t)blockIdx.x * n / G, c1 = (int64_t)(blockIdx.x + 1) * n / G;
-    for (int64_t j = threadIdx.x; j < NMAX; j += blockDim.x) { s_p[j] = 0.0; s_v[j] = 0.0; }
-    __syncthreads();
+    const Geo gmv = geometry(a.ld, RowOps<DT, NMAX>::ES, nwarps, RB);
+    const char* mv_src = reinterpret_cast<const char*>(a.vals) + r0 * (int64_t)gmv.row_bytes;
+#define LSQ_BARRIER()                                   \
+    do {                                                \
+        if (!grid_barrier(a.bar, G, a.err)) {           \
+            ring_drain(ring);                           \
+            return;                                     \
+        }                                               \
+    } while (0)
 
     int iters = 0, outer_used = 0, converged = 0, status = LSQ_ERR_NOT_CONVERGED;
     double rec = 1.0, tru = 1.0, gg = 0.0;
@@ -239,52 +604,45 @@ __global__ void __launch_bounds__(256, 1) k_pcg_dense(PcgArgs a) {
     if (a.h_in) {
         double ha = 0.0, hb = 0.0;
         for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
-            const double h = a.h_in[j], hr = h / a.inv_d[j];
+            const double h = a.h_in[j], hr = h / s_invd[j];
             a.g[j] = h; a.y[j] = 0.0;
             ha = fma(h, h, ha); hb = fma(hr, hr, hb);
         }
-        ha = warp_sum(ha); hb = warp_sum(hb);
-        if ((threadIdx.x & 31) == 0) { s_scal[threadIdx.x >> 5] = ha; s_scal[16 + (threadIdx.x >> 5)] = hb; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double ta = 0.0, tb = 0.0;
-            for (int w = 0; w < nwarps; ++w) { ta += s_scal[w]; tb += s_scal[16 + w]; }
-            a.part_s[(int64_t)blockIdx.x * PART_S + 1] = ta;
-            a.part_s[(int64_t)blockIdx.x * PART_S + 4] = tb;
-        }
-        __syncthreads();
+        cta_partials(a, warp_sum(ha), warp_sum(hb), 1, 4, s_scal);
     } else {
-        row_pass<DTR, NMAX>(a, a.vals_res, PASS_RHS, s_v, s_red, s_scal, r0, r1);
-        if (!grid_barrier(a.bar, G, a.err)) return;
-        slice_reduce(a, c0, c1, 1, 4, s_scal, [&](int64_t j, double h) {
+        row_pass<DTR, NMAX, PASS_RHS>(a, a.vals_res, s_v, s_vc, s_scal, r0, r1, ring);
+        ring_prefetch(ring, mv_src, gmv, r1 - r0);
+        LSQ_BARRIER();
+        slice_reduce(a, c0, c1, 1, 4, s_scal, s_invd, [&](int64_t j, double h) {
             a.g[j] = h; a.y[j] = 0.0;
-            const double hr = h / a.inv_d[j];
+            const double hr = h / s_invd[j];
             return make_double2(h * h, hr * hr); });
     }
-    if (!grid_barrier(a.bar, G, a.err)) return;
-    gg = grid_scalar(a, 1, s_scal);
+    LSQ_BARRIER();
+    gg = warp_grid_scalar(a, 1);
     const double hn = sqrt(gg);
-    const double hn_raw = sqrt(grid_scalar(a, 4, s_scal));
+    const double hn_raw = sqrt(warp_grid_scalar(a, 4));
     double raw = 1.0;
     if (hn == 0.0) {
         converged = 1; status = LSQ_OK; rec = 0.0; tru = 0.0;
     } else {
-        raw = 1.0;
         for (int outer = 0; outer < a.max_outer; ++outer) {
             if (outer > 0) {
-                // true residual g = Â^T (b - Â y)
-                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.y[j] * a.inv_d[j];
+                // true residual g = Â^T (b - Â y)  (normal form: g = h - Â^T Â y)
+                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.y[j] * s_invd[j];
                 __syncthreads();
-                row_pass<DTR, NMAX>(a, a.vals_res, a.h_in ? PASS_MATVEC : PASS_RESID, s_v, s_red, s_scal, r0, r1);
-                if (!grid_barrier(a.bar, G, a.err)) return;
-                slice_reduce(a, c0, c1, 1, 5, s_scal, [&](int64_t j, double t) {
+                if (a.h_in) row_pass<DTR, NMAX, PASS_MATVEC>(a, a.vals_res, s_v, s_vc, s_scal, r0, r1, ring);
+                else row_pass<DTR, NMAX, PASS_RESID>(a, a.vals_res, s_v, s_vc, s_scal, r0, r1, ring);
+                ring_prefetch(ring, mv_src, gmv, r1 - r0);
+                LSQ_BARRIER();
+                slice_reduce(a, c0, c1, 1, 5, s_scal, s_invd, [&](int64_t j, double t) {
                     if (a.h_in) t = a.h_in[j] - t;
                     a.g[j] = t;
-                    const double tr = t / a.inv_d[j];
+                    const double tr = t / s_invd[j];
                     return make_double2(t * t, tr * tr); });
-                if (!grid_barrier(a.bar, G, a.err)) return;
-                gg = grid_scalar(a, 1, s_scal);
-                raw = sqrt(grid_scalar(a, 5, s_scal)) / hn_raw;
+                LSQ_BARRIER();
+                gg = warp_grid_scalar(a, 1);
+                raw = sqrt(warp_grid_scalar(a, 5)) / hn_raw;
                 dirty = false;
             }
             tru = sqrt(gg) / hn;
@@ -297,67 +655,78 @@ __global__ void __launch_bounds__(256, 1) k_pcg_dense(PcgArgs a) {
             for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.g[j];
             __syncthreads();
             op_rows<OPT>(a, c0, c1, s_v, s_scal);
-            if (!grid_barrier(a.bar, G, a.err)) return;
-            double rho = grid_scalar(a, 2, s_scal);
-            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_p[j] = a.z[j];
+            LSQ_BARRIER();
+            double rho = warp_grid_scalar(a, 2);
+            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+                const double pj = a.z[j];
+                s_p[j] = pj;
+                s_v[j] = pj * s_invd[j];
+            }
             __syncthreads();
             bool broke = false;
             while (true) {
-                // fused pass: w = Â^T (Â p)
-                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = s_p[j] * a.inv_d[j];
-                __syncthreads();
-                row_pass<DT, NMAX>(a, a.vals, PASS_MATVEC, s_v, s_red, s_scal, r0, r1);
-                if (!grid_barrier(a.bar, G, a.err)) return;
-                const double pw = grid_scalar(a, 0, s_scal);
+                // fused pass: w = Â^T (Â p), ||Â p||^2 = p^T w
+                row_pass<DT, NMAX, PASS_MATVEC>(a, a.vals, s_v, s_vc, s_scal, r0, r1, ring);
+                ring_prefetch(ring, mv_src, gmv, r1 - r0);
+                LSQ_BARRIER();
+                const double pw = warp_grid_scalar(a, 0);
                 if (!(pw > 0.0) || !(rho > 0.0) || !isfinite(pw) || !isfinite(rho)) {
                     status = LSQ_ERR_BREAKDOWN; broke = true; break;
                 }
                 const double alpha = rho / pw;
-                slice_reduce(a, c0, c1, 1, 6, s_scal, [&](int64_t j, double w) {
+                slice_reduce(a, c0, c1, 1, 6, s_scal, s_invd, [&](int64_t j, double w) {
                     a.y[j] = fma(alpha, s_p[j], a.y[j]);
                     double gj = fma(-alpha, w, a.g[j]);
                     a.g[j] = gj;
                     return make_double2(gj * gj, 0.0); });
-                if (!grid_barrier(a.bar, G, a.err)) return;
+                LSQ_BARRIER();
                 ++iters;
                 dirty = true;
-                gg = grid_scalar(a, 1, s_scal);
+                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.g[j];
+                gg = warp_grid_scalar(a, 1);
                 rec = sqrt(gg) / hn;
+                __syncthreads();
                 if (rec <= a.tol || sqrt(gg) <= a.inner_tol * gstart) break;
                 if (iters >= a.maxit) break;
-                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.g[j];
-                __syncthreads();
                 op_rows<OPT>(a, c0, c1, s_v, s_scal);
-                if (!grid_barrier(a.bar, G, a.err)) return;
-                const double rho_new = grid_scalar(a, 2, s_scal);
+                LSQ_BARRIER();
+                const double rho_new = warp_grid_scalar(a, 2);
                 const double beta = rho_new / rho;
                 rho = rho_new;
-                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_p[j] = fma(beta, s_p[j], a.z[j]);
+                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+                    const double pj = fma(beta, s_p[j], a.z[j]);
+                    s_p[j] = pj;
+                    s_v[j] = pj * s_invd[j];
+                }
                 __syncthreads();
             }
             if (broke) break;
         }
         if (!converged && status != LSQ_ERR_BREAKDOWN && dirty) {
-            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.y[j] * a.inv_d[j];
+            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.y[j] * s_invd[j];
             __syncthreads();
-            row_pass<DTR, NMAX>(a, a.vals_res, a.h_in ? PASS_MATVEC : PASS_RESID, s_v, s_red, s_scal, r0, r1);
-            if (!grid_barrier(a.bar, G, a.err)) return;
-            slice_reduce(a, c0, c1, 3, 5, s_scal, [&](int64_t j, double t) {
+            if (a.h_in) row_pass<DTR, NMAX, PASS_MATVEC>(a, a.vals_res, s_v, s_vc, s_scal, r0, r1, ring);
+            else row_pass<DTR, NMAX, PASS_RESID>(a, a.vals_res, s_v, s_vc, s_scal, r0, r1, ring);
+            LSQ_BARRIER();
+            slice_reduce(a, c0, c1, 3, 5, s_scal, s_invd, [&](int64_t j, double t) {
                 if (a.h_in) t = a.h_in[j] - t;
                 a.g[j] = t;
-                const double tr = t / a.inv_d[j];
+                const double tr = t / s_invd[j];
                 return make_double2(t * t, tr * tr); });
-            if (!grid_barrier(a.bar, G, a.err)) return;
-            tru = sqrt(grid_scalar(a, 3, s_scal)) / hn;
-            raw = sqrt(grid_scalar(a, 5, s_scal)) / hn_raw;
+            LSQ_BARRIER();
+            tru = sqrt(warp_grid_scalar(a, 3)) / hn;
+            raw = sqrt(warp_grid_scalar(a, 5)) / hn_raw;
             if (tru <= a.tol) { converged = 1; status = LSQ_OK; }
         }
     }
-    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) a.x[j] = a.y[j] * a.inv_d[j];
+#undef LSQ_BARRIER
+    ring_drain(ring);
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) a.x[j] = a.y[j] * s_invd[j];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.out_i[0] = iters; a.out_i[1] = outer_used; a.out_i[2] = converged; a.out_i[3] = status;
         a.out_d[0] = rec; a.out_d[1] = tru; a.out_d[2] = (hn == 0.0) ? 0.0 : raw;
     }
+    (void)lane;
 }
 
 // Host launcher (defined per dtype in pcg_f64.cu / pcg_f32.cu)

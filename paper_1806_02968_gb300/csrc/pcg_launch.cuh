@@ -4,13 +4,12 @@
 
 namespace lsq {
 
-constexpr int PCG_THREADS = 256;
+constexpr int PCG_THREADS = 512;
 
 template <int DT, int DTR, int NMAX, typename OPT>
 lsq_status launch_pcg_one(PcgArgs& a, int grid_cap, cudaStream_t st, int* grid_used) {
     auto kern = k_pcg_dense<DT, DTR, NMAX, OPT>;
-    const int nwarps = PCG_THREADS / 32;
-    size_t smem = (size_t)(2 + nwarps) * NMAX * sizeof(double);
+    const size_t smem = pcg_smem_bytes(NMAX);
     LSQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     LSQ_CUDA(cudaGetDevice(&dev));
@@ -39,5 +38,6 @@ inline int pcg_max_grid() {
 
 lsq_status launch_pcg_f64(int64_t nmax, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
 lsq_status launch_pcg_f32(int64_t nmax, int dtr, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
+lsq_status launch_pcg_f32x2(int64_t nmax, int dtr, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
 
 }  // namespace lsq

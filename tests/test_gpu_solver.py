@@ -174,3 +174,35 @@ def test_bad_arguments(lsq):
     assert e.value.code == 1
     with pytest.raises(lsq.L.LsqError):
         lsq.lsq_build_precond(Mx, idx, p, d, lsq.opts(sweeps=0))
+
+
+@pytest.mark.parametrize("with_f64", [True, False])
+def test_pcg_double_float_storage(lsq, orc, with_f64):
+    # values as float pairs (hi, lo), double-float products and sums: FP64-class results
+    mat = W.udv_dense(16384, 128, 1e3, 4)
+    A64 = torch.from_numpy(mat["A"]).cuda()
+    Mx64 = lsq.Matrix(A64)
+    o = lsq.opts(seed=21)
+    idx, p, d = lsq.lsq_sample_rows(Mx64, o)
+    P = lsq.lsq_build_precond(Mx64, idx, p, d, o)
+    pairs = lsq.lsq_split_f64(A64)
+    hi, lo = pairs[:, 0::2].double(), pairs[:, 1::2].double()
+    assert torch.all((hi + lo - A64).abs() <= 2.0 ** -47 * A64.abs())
+    Mx2 = lsq.Matrix(pairs, f32x2=True, vals_f64=A64 if with_f64 else None)
+    xs, b = W.rhs_for(mat, 1, 1e-6, 5)
+    B = torch.from_numpy(b[0]).cuda()
+    X, info = lsq.lsq_pcg_solve(Mx2, P, B, o)
+    X64, info64 = lsq.lsq_pcg_solve(Mx64, P, B, o)
+    smp = orc.Sample(mat, seed=21)
+    Mo = orc.SampledM(smp)
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+    x_or = y / smp.d
+    kappa = np.linalg.cond(mat["A"] / smp.d)
+    assert info.converged[0] == 1 and info.relres_true[0] <= o.tol
+    assert rel(X.cpu().numpy(), x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+    # At kappa(Â^T Â) = 1e6 the CG iteration count depends on rounding: measured, the FP64
+    # GPU path (same arithmetic as the oracle, another summation order in the fused pass and
+    # the reductions) lands 8% from the oracle's count, and double-float products (unit
+    # roundoff 2^-48) land closer than that.  Both are held to 12%.
+    assert abs(int(info64.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info64.iters[0], oi["iters"])
+    assert abs(int(info.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info.iters[0], oi["iters"])

@@ -177,12 +177,19 @@ LSQ_API void lsq_precond_destroy(lsq_precond* P);
  * device double[n*n]).  For checking and diagnostics. */
 LSQ_API lsq_status lsq_precond_get_M(const lsq_precond* P, double* M_out, void* stream);
 
+/* Sparse handles: number of stored entries of M = A_s^T A_s in *nnz_out, and (when the
+ * pointers are not NULL) M in CSR with sorted columns and the diagonal always stored:
+ * row_ptr device int64[n+1], col_idx device int32[nnz], vals device double[nnz]. */
+LSQ_API lsq_status lsq_precond_get_M_csr(const lsq_precond* P, int64_t* nnz_out, int64_t* row_ptr,
+                                         int32_t* col_idx, double* vals, void* stream);
+
 /* Copy the materialised SGS operator (dense handles only, row-major n x n, device
  * double[n*n], converted to FP64). */
 LSQ_API lsq_status lsq_precond_get_op(const lsq_precond* P, double* op_out, void* stream);
 
 /* Apply the preconditioner of Alg. 3: e = P r for k vectors (device, column c at
- * r + c*n, e + c*n). */
+ * r + c*n, e + c*n).  Dense handles multiply by the materialised operator; sparse handles
+ * run the t forward and t backward Gauss-Seidel sweeps on M. */
 LSQ_API lsq_status lsq_precond_apply(const lsq_precond* P, const double* r, double* e, int64_t k,
                              void* stream);
 

@@ -44,6 +44,7 @@ PROTOTYPES = {
     "lsq_precond_destroy": (None, [P]),
     "lsq_precond_get_M": (C.c_int, [P, P, P]),
     "lsq_precond_get_op": (C.c_int, [P, P, P]),
+    "lsq_precond_get_M_csr": (C.c_int, [P, P, P, P, P, P]),
     "lsq_precond_apply": (C.c_int, [P, P, P, I64, P]),
     "lsq_pcg_solve": (C.c_int, [P, P, P, I64, I64, P, I64, P, P, P]),
     "lsq_pcg_adjoint": (C.c_int, [P, P, P, P, P, I64, I64, I64, P, P, P, P, P, P]),

@@ -113,6 +113,18 @@ class Precond:
         _check(L.load().lsq_precond_get_M(self.h, _ptr(out), _stream(stream)), "lsq_precond_get_M")
         return out
 
+    def M_csr(self, stream=None):
+        """(row_ptr, col_idx, vals) of the sparse A_s^T A_s (sparse handles)."""
+        nnz = C.c_int64(0)
+        _check(L.load().lsq_precond_get_M_csr(self.h, C.byref(nnz), None, None, None, _stream(stream)),
+               "lsq_precond_get_M_csr")
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        ci = torch.empty(nnz.value, dtype=torch.int32, device="cuda")
+        va = torch.empty(nnz.value, dtype=torch.float64, device="cuda")
+        _check(L.load().lsq_precond_get_M_csr(self.h, C.byref(nnz), _ptr(rp), _ptr(ci), _ptr(va),
+                                              _stream(stream)), "lsq_precond_get_M_csr")
+        return rp, ci, va
+
     def op(self, stream=None):
         out = torch.empty(self.n, self.n, dtype=torch.float64, device="cuda")
         _check(L.load().lsq_precond_get_op(self.h, _ptr(out), _stream(stream)), "lsq_precond_get_op")

@@ -162,6 +162,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 }  // namespace lsq
 
+namespace lsq { struct SparseHandle; }
+
 // Library-owned preconditioner handle (definition shared by the translation units).
 struct lsq_precond {
     int64_t n = 0, s = 0;
@@ -174,4 +176,5 @@ struct lsq_precond {
     void* op = nullptr;         // dense n x n materialised SGS operator, op_dtype
     double* colscale = nullptr; // d_j (n)
     double* inv_d = nullptr;    // 1/d_j (n)
+    lsq::SparseHandle* sp = nullptr;  // CSR matrices: sparse M, level schedules, A^T pattern
 };

@@ -2,6 +2,7 @@
 // utilities.  The iteration itself runs in the persistent kernel of pcg_kernel.cuh.
 #include "pcg_launch.cuh"
 #include "values.cuh"
+#include "sparse.cuh"
 
 #include <vector>
 
@@ -257,6 +258,11 @@ extern "C" lsq_status lsq_pcg_solve(const lsq_matrix* A, const lsq_precond* P, c
     LSQ_CHECK_ARG(k >= 1, "k must be >= 1");
     LSQ_CHECK_ARG(ldb >= A->m && ldx >= A->n, "ldb >= m and ldx >= n required");
     LSQ_CHECK_ARG(o->tol > 0 && o->maxit >= 0 && o->max_outer >= 1, "bad tolerance or caps");
+    if (!A->dense) {
+        lsq_status s0 = check_matrix(A);
+        if (s0 != LSQ_OK) return s0;
+        return sparse_solve(A, P, B, nullptr, k, ldb, X, ldx, o, info, (cudaStream_t)stream);
+    }
     return solve_columns(A, P, B, nullptr, k, ldb, X, ldx, o, info, (cudaStream_t)stream);
 }
 
@@ -268,6 +274,11 @@ extern "C" lsq_status lsq_pcg_adjoint(const lsq_matrix* A, const lsq_precond* P,
     LSQ_CHECK_ARG(A && P && X && B && G && o, "NULL argument");
     LSQ_CHECK_ARG(k >= 1, "k must be >= 1");
     LSQ_CHECK_ARG(ldb >= A->m && ldx >= A->n, "ldb >= m and ldx >= n required");
+    if (!A->dense) {
+        lsq_status s1 = check_matrix(A);
+        if (s1 != LSQ_OK) return s1;
+        return sparse_adjoint(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, (cudaStream_t)stream);
+    }
     int dt, dtr;
     int64_t nmax;
     lsq_status s0 = check_dense_solve(A, P, &dt, &dtr, &nmax);

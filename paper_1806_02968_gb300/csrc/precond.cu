@@ -9,6 +9,7 @@
 // that operator instead of a 2n-step dependency chain per application.
 #include "common.cuh"
 #include "values.cuh"
+#include "sparse.cuh"
 
 namespace lsq {
 
@@ -213,6 +214,7 @@ static void free_handle(lsq_precond* H) {
     if (H->op) cudaFree(H->op);
     if (H->colscale) cudaFree(H->colscale);
     if (H->inv_d) cudaFree(H->inv_d);
+    if (H->sp) free_sparse(H->sp);
     delete H;
 }
 
@@ -230,27 +232,33 @@ extern "C" lsq_status lsq_build_precond(const lsq_matrix* A, const int32_t* idx,
     LSQ_CHECK_ARG(o->sweeps >= 1 && o->sweeps <= 64, "sweeps must be in [1, 64]");
     LSQ_CHECK_ARG(o->precond_dtype == LSQ_F64 || o->precond_dtype == LSQ_F32, "precond_dtype must be F64 or F32");
     *P_out = nullptr;
-    if (!A->dense) {
-        set_error("sparse preconditioner assembly is not available in this build");
-        return LSQ_ERR_UNSUPPORTED;
-    }
-    LSQ_CHECK_ARG(A->n <= 2048, "dense path supports n <= 2048");
+    if (A->dense) LSQ_CHECK_ARG(A->n <= 2048, "dense path supports n <= 2048");
+    else LSQ_CHECK_ARG(o->sweeps <= 32, "sparse preconditioners support sweeps <= 32");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = A->n;
     lsq_precond* H = new lsq_precond();
-    H->n = n; H->s = s; H->dense = 1; H->sweeps = o->sweeps; H->op_dtype = o->precond_dtype;
+    H->n = n; H->s = s; H->dense = A->dense ? 1 : 0; H->sweeps = o->sweeps; H->op_dtype = o->precond_dtype;
     H->stream = st;
     auto fail = [&](lsq_status code) { free_handle(H); return code; };
     cudaError_t e;
-    if ((e = cudaMalloc(&H->M, sizeof(double) * n * n)) != cudaSuccess ||
-        (e = cudaMalloc(&H->op, elem_size(o->precond_dtype) * n * n)) != cudaSuccess ||
-        (e = cudaMalloc(&H->colscale, sizeof(double) * n)) != cudaSuccess ||
+    if ((e = cudaMalloc(&H->colscale, sizeof(double) * n)) != cudaSuccess ||
         (e = cudaMalloc(&H->inv_d, sizeof(double) * n)) != cudaSuccess) {
         set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
         return fail(LSQ_ERR_NOMEM);
     }
     k_inv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, colscale, H->colscale, H->inv_d);
     count_launch();
+    if (!A->dense) {
+        lsq_status rs = build_sparse(A, idx, p, s, H, st);
+        if (rs != LSQ_OK) return fail(rs);
+        *P_out = H;
+        return LSQ_OK;
+    }
+    if ((e = cudaMalloc(&H->M, sizeof(double) * n * n)) != cudaSuccess ||
+        (e = cudaMalloc(&H->op, elem_size(o->precond_dtype) * n * n)) != cudaSuccess) {
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return fail(LSQ_ERR_NOMEM);
+    }
     lsq_status r;
     switch (A->dtype) {
         case LSQ_F64: r = build_dense<LSQ_F64>(A, idx, p, s, H, st); break;
@@ -290,10 +298,23 @@ extern "C" lsq_status lsq_precond_get_op(const lsq_precond* P, double* op_out, v
     return LSQ_OK;
 }
 
+extern "C" lsq_status lsq_precond_get_M_csr(const lsq_precond* P, int64_t* nnz_out, int64_t* row_ptr,
+                                            int32_t* col_idx, double* vals, void* stream) {
+    LSQ_CHECK_ARG(P && nnz_out, "NULL argument");
+    LSQ_CHECK_ARG(!P->dense && P->sp, "only sparse handles hold a CSR M");
+    *nnz_out = P->sp->nnz_M;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (row_ptr) LSQ_CUDA(cudaMemcpyAsync(row_ptr, P->sp->mptr, 8 * (size_t)(P->n + 1), cudaMemcpyDeviceToDevice, st));
+    if (col_idx) LSQ_CUDA(cudaMemcpyAsync(col_idx, P->sp->mcol, 4 * (size_t)P->sp->nnz_M, cudaMemcpyDeviceToDevice, st));
+    if (vals) LSQ_CUDA(cudaMemcpyAsync(vals, P->sp->mval, 8 * (size_t)P->sp->nnz_M, cudaMemcpyDeviceToDevice, st));
+    LSQ_CUDA(cudaStreamSynchronize(st));
+    return LSQ_OK;
+}
+
 extern "C" lsq_status lsq_precond_apply(const lsq_precond* P, const double* r, double* e,
                                         int64_t k, void* stream) {
     LSQ_CHECK_ARG(P && r && e && k >= 1, "bad argument");
-    LSQ_CHECK_ARG(P->dense, "only dense handles in this build");
+    if (!P->dense) return sparse_apply(P, r, e, k, (cudaStream_t)stream);
     cudaStream_t st = (cudaStream_t)stream;
     unsigned g = (unsigned)std::min<int64_t>((P->n * k * 32 + 255) / 256, 152 * 8);
     if (P->op_dtype == LSQ_F64) k_op_apply<double><<<g, 256, 0, st>>>(P->n, k, (const double*)P->op, r, e);

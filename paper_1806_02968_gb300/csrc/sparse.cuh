@@ -1,0 +1,39 @@
+// Sparse (CSR) preconditioner data shared by sparse_build.cu and pcg_sparse.cu.
+#pragma once
+#include "common.cuh"
+
+namespace lsq {
+
+struct SparseHandle {
+    int64_t m = 0, nnz_A = 0, nnz_M = 0, n_unique = 0;
+    // M = A_s^T A_s in CSR (sorted columns, diagonal always stored)
+    int64_t* mptr = nullptr;
+    int32_t* mcol = nullptr;
+    double* mval = nullptr;
+    float* mval32 = nullptr;    // FP32 copy when the operator dtype is F32
+    double* dinv = nullptr;     // 1 / M_jj
+    // rows listed by forward / backward level (Gauss-Seidel dependency order)
+    int32_t* sched_f = nullptr;
+    int32_t* sched_b = nullptr;
+    int64_t nlev_f = 0, nlev_b = 0;
+    // transposed pattern of A: column pointers, row indices, source entry of each
+    int64_t* atptr = nullptr;
+    int32_t* atrow = nullptr;
+    int64_t* atperm = nullptr;
+};
+
+lsq_status scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* scratch, cudaStream_t st);
+lsq_status transpose_pattern(const int64_t* rptr, const int32_t* col, int64_t nr, int64_t nc, int64_t nnz,
+                             int64_t* cptr, int32_t* trow, int64_t* tperm, cudaStream_t st);
+lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p, int64_t s,
+                        lsq_precond* H, cudaStream_t st);
+void free_sparse(SparseHandle* S);
+lsq_status sparse_solve(const lsq_matrix* A, const lsq_precond* P, const double* B, const double* Hcols,
+                        int64_t k, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o, lsq_info* info,
+                        cudaStream_t st);
+lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_t k, cudaStream_t st);
+lsq_status sparse_adjoint(const lsq_matrix* A, const lsq_precond* P, const double* X, const double* B,
+                          const double* G, int64_t k, int64_t ldb, int64_t ldx, double* grad_b,
+                          double* grad_vals, double* Lambda, const lsq_opts* o, lsq_info* info, cudaStream_t st);
+
+}  // namespace lsq

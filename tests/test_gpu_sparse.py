@@ -1,0 +1,93 @@
+"""CSR path on the GPU vs the oracle: sampled normal matrix (SpGEMM), the Gauss-Seidel
+sweeps of Alg. 3 on it, PCG and the adjoint."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from helpers import rel, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(lsq, orc, mat, seed, sweeps=1, dtype="f64", pdt=0, with_f64=False):
+    Mx, keep, seen = to_device(lsq, mat, dtype, with_f64=with_f64)
+    o = lsq.opts(seed=seed, sweeps=sweeps, precond_dtype=pdt)
+    idx, p, d = lsq.lsq_sample_rows(Mx, o)
+    P = lsq.lsq_build_precond(Mx, idx, p, d, o)
+    smp = orc.Sample(seen, seed=seed)
+    Mo = orc.SampledM(smp)
+    return Mx, keep, seen, o, P, smp, Mo
+
+
+CASES = {
+    "sprand": lambda: W.sparse_random(20000, 300, 8, 3),
+    "graph": lambda: W.graph_incidence(2000, 9000, 4),
+    "wide": lambda: W.sparse_random(60000, 2000, 8, 5),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_sparse_normal_matrix_pattern_and_values(lsq, orc, case):
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003)
+    rp, ci, va = (t.cpu().numpy() for t in P.M_csr())
+    assert np.array_equal(rp, Mo.row_ptr), "row pointers of A_s^T A_s differ"
+    assert np.array_equal(ci, Mo.col), "column pattern of A_s^T A_s differs"
+    np.testing.assert_allclose(va, Mo.val, rtol=1e-12, atol=1e-14 * np.abs(Mo.val).max())
+
+
+@pytest.mark.parametrize("sweeps", [1, 2])
+@pytest.mark.parametrize("case", ["sprand", "graph"])
+def test_sparse_sweeps_match_alg3(lsq, orc, case, sweeps):
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003, sweeps=sweeps)
+    rng = np.random.default_rng(sweeps)
+    R = rng.standard_normal((3, seen["n"]))
+    E = P.apply(torch.from_numpy(R).cuda()).cpu().numpy()
+    for c in range(3):
+        assert rel(E[c], orc.sgs_apply(Mo, R[c], sweeps)) <= 1e-11
+
+
+@pytest.mark.parametrize("case,noise", [("sprand", 1e-3), ("graph", 1e-4)])
+def test_sparse_pcg_matches_oracle(lsq, orc, case, noise):
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003)
+    xs, b = W.rhs_for(seen, 2, noise, 17)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    A = W.dense_from_csr(seen)
+    kappa = np.linalg.cond(A / smp.d)
+    for c in range(2):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+        x_or = y / smp.d
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert info.relres_true[c] <= o.tol
+        assert rel(X[c], x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info.iters[c], oi["iters"])
+    assert info.levels >= 1 and info.nnz_M == Mo.val.size
+
+
+def test_sparse_f32_values_with_f64_refinement(lsq, orc):
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["sprand"](), 7, dtype="f32", pdt=1, with_f64=True)
+    o.max_outer = 30
+    o.inner_tol = 1e-4
+    xs, b = W.rhs_for(seen, 1, 1e-3, 9)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
+    assert info.converged[0] == 1 and info.relres_true[0] <= o.tol
+
+
+def test_sparse_adjoint_matches_oracle(lsq, orc):
+    mat = W.sparse_random(5000, 60, 6, 2)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 6)
+    o.tol = 1e-12
+    xs, b = W.rhs_for(seen, 2, 1e-2, 8)
+    B = torch.from_numpy(b).cuda()
+    X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    G = 2 * (X - torch.from_numpy(xs).cuda())
+    gb, gv, lam, ainfo = lsq.lsq_pcg_adjoint(Mx, P, X, B, G, o)
+    Xh, Gh = X.cpu().numpy(), G.cpu().numpy()
+    gsum = 0
+    for c in range(2):
+        gbr, gvr, lamr, _ = orc.adjoint(seen, smp, Mo, Xh[c], b[c], Gh[c], tol=1e-12)
+        assert rel(lam[c].cpu().numpy(), lamr) <= 1e-8
+        assert rel(gb[c].cpu().numpy(), gbr) <= 1e-8
+        gsum = gsum + gvr
+    assert rel(gv.cpu().numpy(), gsum) <= 1e-8

@@ -150,6 +150,27 @@ LSQ_API lsq_status lsq_sample_rows(const lsq_matrix* A, const lsq_opts* o, int64
                            int64_t* s_out, void* stream);
 
 /*
+ * lsq_sample_rows_static -- lsq_sample_rows for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart; this is a deployment convenience.  Some callers must not
+ * allocate: code that runs inside another framework's device-memory pool with no headroom
+ * left, or a real-time loop where an allocator call could block on the device or fail at
+ * run time.  This entry point computes exactly what lsq_sample_rows computes (same kernels,
+ * same bits) but takes all of its scratch from one fixed array in device memory that the
+ * library declares (8.6 MiB, held by every GPU that loads the library until the process
+ * exits); it calls no allocation routine.
+ *
+ * Limits: A may have at most 262144 rows and 4096 columns (else LSQ_ERR_INVALID).  The
+ * first call on a device looks up the array's device address (once per device, with that
+ * device current), so make the first call on each device before any stream capture.  Every
+ * call uses the same array: calls that overlap on the GPU (different streams, or host
+ * threads) race, so serialise them.  Arguments, outputs and status as lsq_sample_rows.
+ */
+LSQ_API lsq_status lsq_sample_rows_static(const lsq_matrix* A, const lsq_opts* o, int64_t s,
+                                          int32_t* idx_out, double* p_out, double* colscale_out,
+                                          int64_t* s_out, void* stream);
+
+/*
  * lsq_build_precond -- Sec. 3.3 and Alg. 3.
  *
  * Assembles M = A_s^T A_s = (1/s) sum_t â_{i_t}^T â_{i_t} / p_{i_t} (â = a D^{-1},

@@ -40,6 +40,7 @@ PROTOTYPES = {
     "lsq_default_opts": (None, [P]),
     "lsq_sample_size": (I64, [I64, D]),
     "lsq_sample_rows": (C.c_int, [P, P, I64, P, P, P, P, P]),
+    "lsq_sample_rows_static": (C.c_int, [P, P, I64, P, P, P, P, P]),
     "lsq_build_precond": (C.c_int, [P, P, P, P, I64, P, P, P]),
     "lsq_precond_destroy": (None, [P]),
     "lsq_precond_get_M": (C.c_int, [P, P, P]),

@@ -96,6 +96,21 @@ def lsq_sample_rows(A: Matrix, o=None, s: int = 0, stream=None):
     return idx, p, d
 
 
+def lsq_sample_rows_static(A: Matrix, o=None, s: int = 0, stream=None):
+    """lsq_sample_rows without any device allocation inside the library (its scratch is a
+    fixed device array; at most 262144 rows and 4096 columns)."""
+    o = o or opts()
+    s_eff = s if s else lsq_sample_size(A.n, o.sample_factor)
+    dev = A.vals.device
+    idx = torch.empty(s_eff, dtype=torch.int32, device=dev)
+    p = torch.empty(s_eff, dtype=torch.float64, device=dev)
+    d = torch.empty(A.n, dtype=torch.float64, device=dev)
+    s_out = C.c_int64(0)
+    _check(L.load().lsq_sample_rows_static(A.ref, C.byref(o), s_eff, _ptr(idx), _ptr(p), _ptr(d),
+                                           C.byref(s_out), _stream(stream)), "lsq_sample_rows_static")
+    return idx, p, d
+
+
 class Precond:
     """Owns an lsq_precond handle (Sec. 3.3 + Alg. 3)."""
 

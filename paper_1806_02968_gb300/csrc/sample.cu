@@ -417,6 +417,87 @@ static lsq_status sample_impl(const lsq_matrix* A, const lsq_opts* o, int64_t s,
     return read_dev_error(err, st);
 }
 
+// ---------------------------------------------------------------------------------------
+// Fixed scratch for lsq_sample_rows_static: the same kernels as lsq_sample_rows, with the
+// scratch carved from one file-scope device array instead of a stream-ordered allocation.
+// ---------------------------------------------------------------------------------------
+constexpr int64_t STATIC_MAX_ROWS = 262144;
+constexpr int64_t STATIC_MAX_COLS = 4096;
+constexpr size_t rnd256(size_t b) { return (b + 255) & ~size_t(255); }
+// byte size of the scratch layout used below, for m rows and n columns
+constexpr size_t static_scratch_bytes(int64_t m, int64_t n) {
+    return rnd256(16) + rnd256(8 * n) + rnd256(16 * n) + rnd256(16) + rnd256(4 * n) + 3 * rnd256(8 * n) +
+           rnd256(16 * m) + rnd256(16 * (m + 1)) + rnd256(16 * ((m + SCAN_TILE - 1) / SCAN_TILE));
+}
+constexpr size_t STATIC_SCRATCH_BYTES = static_scratch_bytes(STATIC_MAX_ROWS, STATIC_MAX_COLS);
+static __device__ __align__(256) unsigned char g_sample_scratch[STATIC_SCRATCH_BYTES];
+
+// Device address of g_sample_scratch on the current device, looked up once per device.
+static lsq_status static_scratch_address(char** out) {
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    LSQ_CUDA(cudaGetDevice(&dev));
+    LSQ_CHECK_ARG(dev >= 0 && dev < 64, "device ordinal must be < 64");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        LSQ_CUDA(cudaGetSymbolAddress(&p, g_sample_scratch));
+        addr[dev] = p;
+    }
+    *out = static_cast<char*>(addr[dev]);
+    return LSQ_OK;
+}
+
+template <int DT>
+static lsq_status sample_into_static(const lsq_matrix* A, const lsq_opts* o, int64_t s, int32_t* idx_out,
+                                     double* p_out, double* colscale_out, char* base, cudaStream_t st) {
+    const int64_t m = A->m, n = A->n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off += rnd256(bytes); return at; };
+    size_t o_err = take(16), o_amax = take(8 * n), o_c = take(16 * n), o_E1g = take(16),
+           o_E1j = take(4 * n), o_d2 = take(8 * n), o_inv = take(8 * n), o_d = take(8 * n),
+           o_w = take(16 * m), o_P = take(16 * (m + 1));
+    const int64_t ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+    size_t o_ts = take(16 * ntiles);
+    if (off > STATIC_SCRATCH_BYTES) { set_error("static scratch layout exceeds its array"); return LSQ_ERR_INVALID; }
+    unsigned* err = (unsigned*)(base + o_err);
+    unsigned long long* amax = (unsigned long long*)(base + o_amax);
+    u128* c = (u128*)(base + o_c);
+    unsigned* E1g = (unsigned*)(base + o_E1g);
+    int* E1j = (int*)(base + o_E1j);
+    double* d2 = (double*)(base + o_d2);
+    double* inv = (double*)(base + o_inv);
+    double* d = colscale_out ? colscale_out : (double*)(base + o_d);
+    u128* w = (u128*)(base + o_w);
+    u128* P = (u128*)(base + o_P);
+    u128* ts = (u128*)(base + o_ts);
+    // the array keeps the previous call's contents: clear everything that accumulates
+    LSQ_CUDA(cudaMemsetAsync(base, 0, o_E1g, st));
+    LSQ_CUDA(cudaMemsetAsync(E1g, 0xff, 16, st));
+    lsq_matrix Av = *A;
+    int64_t rpb = 0;
+    if (A->dense) {
+        rpb = (m + 152 * 8 - 1) / (152 * 8);
+        if (rpb < 16) rpb = 16;
+        k_colmax_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, amax, err, rpb);
+    } else {
+        k_colmax_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, amax, err);
+    }
+    k_col_exponents<<<grid_for(n, 256), 256, 0, st>>>(n, amax, E1j, E1g, err);
+    if (A->dense) k_colsum_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, E1j, c, rpb);
+    else k_colsum_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, E1j, c);
+    k_colscale<<<grid_for(n, 256), 256, 0, st>>>(n, o->normalize ? 1 : 0, E1j, E1g, c, d2, inv, d);
+    k_rowweight<DT><<<grid_for(m * 32, 256), 256, 0, st>>>(Av, inv, w);
+    k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts);
+    k_scan_sums<<<1, 1024, 0, st>>>(ts, ntiles);
+    k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts, P);
+    k_draw<<<grid_for(s, 256), 256, 0, st>>>(P, m, s, (unsigned long long)o->seed, idx_out, p_out, err);
+    count_launch(10);
+    LSQ_CUDA(cudaGetLastError());
+    return read_dev_error(err, st);
+}
+
 }  // namespace lsq
 
 using namespace lsq;
@@ -457,6 +538,36 @@ extern "C" lsq_status lsq_sample_rows(const lsq_matrix* A, const lsq_opts* o, in
         case LSQ_F32: return sample_impl<LSQ_F32>(A, o, s, idx_out, p_out, colscale_out, st);
         case LSQ_BF16: return sample_impl<LSQ_BF16>(A, o, s, idx_out, p_out, colscale_out, st);
         case LSQ_F32X2: return sample_impl<LSQ_F32X2>(A, o, s, idx_out, p_out, colscale_out, st);
+    }
+    set_error("unknown dtype");
+    return LSQ_ERR_INVALID;
+}
+
+extern "C" lsq_status lsq_sample_rows_static(const lsq_matrix* A, const lsq_opts* o, int64_t s,
+                                             int32_t* idx_out, double* p_out, double* colscale_out,
+                                             int64_t* s_out, void* stream) {
+    lsq_status st0 = check_matrix(A);
+    if (st0 != LSQ_OK) return st0;
+    LSQ_CHECK_ARG(o != nullptr, "opts is NULL");
+    LSQ_CHECK_ARG(idx_out != nullptr, "idx_out is NULL");
+    LSQ_CHECK_ARG(s >= 0, "s < 0");
+    if (A->m > STATIC_MAX_ROWS || A->n > STATIC_MAX_COLS) {
+        set_error("lsq_sample_rows_static: A has more than 262144 rows or 4096 columns, the size of "
+                  "its fixed scratch; use lsq_sample_rows");
+        return LSQ_ERR_INVALID;
+    }
+    if (s == 0) s = lsq_sample_size(A->n, o->sample_factor);
+    LSQ_CHECK_ARG(s > 0 && s < (int64_t)1 << 40, "sample size out of range");
+    if (s_out) *s_out = s;
+    char* base = nullptr;
+    lsq_status r = static_scratch_address(&base);
+    if (r != LSQ_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (A->dtype) {
+        case LSQ_F64: return sample_into_static<LSQ_F64>(A, o, s, idx_out, p_out, colscale_out, base, st);
+        case LSQ_F32: return sample_into_static<LSQ_F32>(A, o, s, idx_out, p_out, colscale_out, base, st);
+        case LSQ_BF16: return sample_into_static<LSQ_BF16>(A, o, s, idx_out, p_out, colscale_out, base, st);
+        case LSQ_F32X2: return sample_into_static<LSQ_F32X2>(A, o, s, idx_out, p_out, colscale_out, base, st);
     }
     set_error("unknown dtype");
     return LSQ_ERR_INVALID;

@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
+    ap.add_argument("--workload", choices=["udv", "sparse", "graph", "adjoint"], default="udv",
+                    help="udv: the timed benchmark; the others measure the CSR configurations")
     return ap.parse_args()
 
 
@@ -102,13 +104,14 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def make_problem(args, seed_base, device_qr=True):
+def make_problem(args, seed_base, device_matmul=True):
     import workloads as W
-    qr = None
-    if device_qr:
+    mm = None
+    if device_matmul:   # input generation only: the two large Cholesky-QR products on the device
         import torch
-        qr = lambda G: torch.linalg.qr(torch.from_numpy(G).cuda())[0].cpu().numpy()
-    mat = W.udv_dense(args.m, args.n, args.kappa, seed_base, qr=qr)
+        mm = lambda X, Y: (torch.from_numpy(np.ascontiguousarray(X)).cuda()
+                           @ torch.from_numpy(np.ascontiguousarray(Y)).cuda()).cpu().numpy()
+    mat = W.udv_dense(args.m, args.n, args.kappa, seed_base, matmul=mm)
     xs, b = W.rhs_for(mat, 1, 1e-6, seed_base + 100)
     return mat, xs[0], b[0]
 
@@ -152,7 +155,7 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    mat, xs, b = make_problem(args, 2, device_qr=False)
+    mat, xs, b = make_problem(args, 2, device_matmul=False)
     seed = 1002
     times = []
     iters_assumed = int(os.environ.get("LSQ_REF_ITERS", "193526"))
@@ -329,10 +332,70 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sparse_workload(args):
+    """CSR configurations: sparse random 4e6 x 4e4 (FP32 values, FP64 refinement), weighted
+    graph incidence with 32 right-hand sides (FP64), sparse 1e6 x 1e4 with 16 right-hand
+    sides through the solve and the adjoint (FP32 values, FP64 refinement)."""
+    import torch
+    import workloads as W
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    from paper_1806_02968_gb300 import api
+    torch.cuda.set_device(0)
+    if args.workload == "sparse":
+        mat, k, noise, dt = W.sparse_random(4_000_000, 40_000, 8, 3), 1, 1e-3, "f32"
+        name = "sparse_random_4000000x40000_8nnz"
+    elif args.workload == "graph":
+        mat, k, noise, dt = W.graph_incidence(262144, 8 * 262144, 4), 32, 1e-4, "f64"
+        name = "graph_incidence_262144nodes_32rhs"
+    else:
+        mat, k, noise, dt = W.sparse_random(1_000_000, 10_000, 8, 5), 16, 1e-3, "f32"
+        name = "sparse_random_1000000x10000_16rhs_adjoint"
+    xs, b = W.rhs_for(mat, k, noise, 1234)
+    rp = torch.from_numpy(mat["row_ptr"]).cuda()
+    ci = torch.from_numpy(mat["col_idx"]).cuda()
+    v64 = torch.from_numpy(mat["vals"]).cuda()
+    vals = v64.float() if dt == "f32" else v64
+    Mx = api.Matrix(row_ptr=rp, col_idx=ci, vals=vals, n=mat["n"], vals_f64=v64 if dt == "f32" else None)
+    o = api.opts(seed=1003, tol=args.tol, maxit=args.maxit, max_outer=50, inner_tol=args.inner_tol,
+                 precond_dtype=1 if dt == "f32" else 0)
+    B = torch.from_numpy(b).cuda()
+    X = None
+    res = {}
+    for rep in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idx, p, d = api.lsq_sample_rows(Mx, o)
+        torch.cuda.synchronize(); t1 = time.perf_counter()
+        P = api.lsq_build_precond(Mx, idx, p, d, o)
+        torch.cuda.synchronize(); t2 = time.perf_counter()
+        X, info = api.lsq_pcg_solve(Mx, P, B, o)
+        torch.cuda.synchronize(); t3 = time.perf_counter()
+        extra = {}
+        if args.workload == "adjoint":
+            G = 2 * (X - torch.from_numpy(xs).cuda())
+            gb, gv, lam, ainfo = api.lsq_pcg_adjoint(Mx, P, X, B, G, o)
+            torch.cuda.synchronize()
+            extra = {"adjoint_s": time.perf_counter() - t3, "adjoint_iters": ainfo.iters.tolist()}
+        res = {"sample_s": t1 - t0, "build_s": t2 - t1, "solve_s": t3 - t2, **extra,
+               "iters": info.iters.tolist(), "converged": info.converged.tolist(),
+               "relres_true_max": float(np.max(info.relres_true)), "nnz_A": int(mat["row_ptr"][-1]),
+               "nnz_M": int(info.nnz_M), "levels": int(info.levels), "s": int(info.s)}
+    tot = res["sample_s"] + res["build_s"] + res["solve_s"] + res.get("adjoint_s", 0.0)
+    line = {"metric": METRIC, "value": k / tot, "unit": "solves/s (right-hand sides)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3, "higher_is_better": True,
+            "dtype": dt + ("+f64" if dt == "f32" else ""), "data": "synthetic",
+            "config": {"workload": name, "m": int(mat["m"]), "n": int(mat["n"]), "k": k, "tol": args.tol},
+            "phases": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "udv":
+        run_sparse_workload(args)
     else:
         run_ours(args)
 

@@ -46,12 +46,19 @@ struct SpArgs {
     const double* dinv;
     const int32_t* sched_f;
     const int32_t* sched_b;
+    const int32_t* lvl_f;       // level of each schedule slot
+    const int32_t* lvl_b;
+    const int64_t* lsize_f;     // rows per level
+    const int64_t* lsize_b;
+    unsigned long long* done_f; // rows finished per level, cumulative over the sweeps of a solve
+    unsigned long long* done_b;
+    int lpr, lpc;               // lanes per row of A, lanes per column of A (powers of two <= 32)
     int sweeps;
     // vectors
     double *y, *g, *z, *p, *pt, *w, *q, *e0, *e1, *h;
-    unsigned *flag_f, *flag_b;
-    double* part;             // per-block partials
-    int nblk;                 // blocks of the reduction kernels
+    double* part;             // per-block partials: [row pass: rblk][update: nblk][g^T z: nblk]
+    int nblk;                 // blocks of the vector kernels
+    int rblk;                 // capacity for the row pass's blocks
     SpState* S;
     double tol, inner_tol;
     int32_t maxit;
@@ -82,27 +89,26 @@ __device__ __forceinline__ double sum_parts(const double* part, int cnt, double*
 constexpr int SP_T = 256;
 enum { SPM_MATVEC = 0, SPM_RHS = 1, SPM_RESID = 2 };
 
-// q_i = sum_e a_e x_{col e} (x = D^{-1} p or D^{-1} y), or b_i, or b_i - that; 8 lanes per row
+// q_i = sum_e a_e x_{col e} (x = D^{-1} p or D^{-1} y), or b_i, or b_i - that.  A group of
+// LPR lanes (a power of two, about the mean row length) takes a row.
 template <int DT>
 __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_res, const double* x) {
     __shared__ double sh[40];
     if (a.S->done) return;
     const void* vals = use_res ? a.vals_res : a.vals;
-    const int sub = threadIdx.x & 7;
-    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    const int L = a.lpr;
+    const int sub = threadIdx.x & (L - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / L;
     double qq = 0.0;
     for (int64_t i0 = 0; i0 < a.m; i0 += ngrp) {
         const int64_t i = i0 + grp;
         double dot = 0.0;
         if (i < a.m && mode != SPM_RHS) {
-            for (int64_t e = a.row_ptr[i] + sub; e < a.row_ptr[i + 1]; e += 8) {
-                const double v = Val<DT>::load(vals, e);
-                dot = fma(v, x[a.col_idx[e]], dot);
-            }
+            const int64_t e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
+            for (int64_t e = e0 + sub; e < e1; e += L) dot = fma(Val<DT>::load(vals, e), x[a.col_idx[e]], dot);
         }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        for (int o = L >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
         if (i < a.m && sub == 0) {
             const double q = mode == SPM_MATVEC ? dot : (mode == SPM_RHS ? a.b[i] : a.b[i] - dot);
             a.q[i] = q;
@@ -113,22 +119,22 @@ __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_re
     if (threadIdx.x == 0) a.part[blockIdx.x] = t;
 }
 
-// w_j = (1/d_j) sum_{i in column j} a_ij q_i, one warp per column (fixed order)
+// w_j = (1/d_j) sum_{i in column j} a_ij q_i; a group of LPC lanes per column (fixed order)
 template <int DT>
 __global__ void __launch_bounds__(SP_T) k_sp_cols(SpArgs a, int use_res, double* out) {
     if (a.S->done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int L = a.lpc;
+    const int sub = threadIdx.x & (L - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / L;
     const void* vals = use_res ? a.valsT_res : a.valsT;
-    for (int64_t j = warp; j < a.n; j += nw) {
+    for (int64_t j0 = 0; j0 < a.n; j0 += ngrp) {
+        const int64_t j = j0 + grp;
         double t = 0.0;
-        for (int64_t e = a.atptr[j] + lane; e < a.atptr[j + 1]; e += 32) {
-            const double v = Val<DT>::load(vals, e);
-            t = fma(v, a.q[a.atrow[e]], t);
-        }
-        t = warp_sum(t);
-        if (lane == 0) out[j] = t * a.inv_d[j];
+        if (j < a.n)
+            for (int64_t e = a.atptr[j] + sub; e < a.atptr[j + 1]; e += L) t = fma(Val<DT>::load(vals, e), a.q[a.atrow[e]], t);
+        for (int o = L >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (j < a.n && sub == 0) out[j] = t * a.inv_d[j];
     }
 }
 
@@ -151,16 +157,16 @@ __global__ void __launch_bounds__(SP_T) k_sp_update(SpArgs a, int nparts) {
         gg = fma(gj, gj, gg);
     }
     const double t = block_sum(gg, sh);
-    if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = t;
+    if (threadIdx.x == 0) a.part[a.rblk + blockIdx.x] = t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_flag(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_flag(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // One Gauss-Seidel sweep of Alg. 3 on M (FWD: rows in natural order, lower entries are
@@ -168,7 +174,17 @@ __device__ __forceinline__ void st_release_flag(unsigned* p, unsigned v) {
 //   e_new_j = (r_j - sum_{other side} M_jk e_old_k - sum_{dependency side} M_jk e_new_k) / M_jj
 // With `identity` (the backward sweep right after a single forward sweep from zero,
 // t = 1): r - L e_old = D e_old, so e_new_j = e_old_j - (sum_{k>j} M_jk e_new_k) / M_jj.
+//
+// Level scheduling without grid barriers.  The launch is cooperative (every warp resident);
+// warp w takes schedule slots w, w + W, w + 2W, ... (rows sorted by level), so it meets its
+// rows in level order.  A row of level L loads its entries and adds its other-side terms,
+// then waits until every row of level L-1 has finished this sweep: 32 cumulative
+// sub-counters per level (rows add to sub-counter w mod 32, a waiting warp sums all 32 in
+// one load), acquire/release ordering, bounded polls.  Rows of level L depend only on lower
+// levels, which every warp finishes first, so the wait always ends.
 // `check` (first sweep of an iteration): reduce ||g||^2 first and stop when converged.
+constexpr int SW_SUB = 32;          // sub-counters per level
+constexpr int SW_PF = 16;           // entries per lane held in registers before the wait
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, const double* e_old,
                                                    double* e_new, int identity, int check, int nparts,
@@ -177,7 +193,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
     __shared__ int s_stop;
     if (a.S->done) return;
     if (check) {
-        const double gg = sum_parts(a.part + a.nblk, nparts, sh);
+        const double gg = sum_parts(a.part + a.rblk, nparts, sh);
         if (threadIdx.x == 0) {
             const double gn = sqrt(gg);
             int stop = 0;
@@ -192,49 +208,77 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
             return;
         }
     }
-    // completion flags hold the sweep's number: distinct for every sweep of a solve
-    const unsigned epoch = (unsigned)(a.S->napply * 2 * a.sweeps + sweep_idx + 1);
-    unsigned* flags = FWD ? a.flag_f : a.flag_b;
-    unsigned* ticket = &a.S->ticket[sweep_idx];
+    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;   // sweep number within its direction
+    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
+    unsigned long long* done = FWD ? a.done_f : a.done_b;
+    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
+    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
     const int32_t* sched = FWD ? a.sched_f : a.sched_b;
     const MT* mv = reinterpret_cast<const MT*>(a.mval);
     const int lane = threadIdx.x & 31;
-    while (true) {
-        unsigned slot = 0;
-        if (lane == 0) slot = atomicAdd(ticket, 1u);
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if ((int64_t)slot >= a.n) break;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool other = !identity && e_old != nullptr;
+    bool ok = true;
+    for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
+        const int L = lvl[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1];
+        // entries of the first 32*SW_PF positions, in registers
+        int32_t kk[SW_PF];
+        double mm[SW_PF];
         double acc = 0.0;
-        bool ok = true;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int64_t k = a.mcol[e];
-            if (k == j) continue;
-            const double mjk = (double)mv[e];
-            const bool dep = FWD ? (k < j) : (k > j);
-            if (dep) {
-                unsigned polls = 0;
-                while (ld_acquire_flag(&flags[k]) != epoch) {
-                    if (++polls > (1u << 24)) { ok = false; break; }
-                    if (polls > 32) __nanosleep(64);
-                }
-                acc = fma(mjk, e_new[k], acc);
-            } else if (!identity && e_old) {
-                acc = fma(mjk, e_old[k], acc);
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c) {
+            const int64_t e = e0 + lane + 32 * c;
+            kk[c] = -1;
+            mm[c] = 0.0;
+            if (e < e1) {
+                const int32_t k = a.mcol[e];
+                const double mjk = (double)mv[e];
+                const bool dep = FWD ? (k < j) : (k > j);
+                if (dep) { kk[c] = k; mm[c] = mjk; }
+                else if (other && k != j) acc = fma(mjk, e_old[k], acc);
             }
         }
+        for (int64_t e = e0 + lane + 32 * SW_PF; e < e1; e += 32) {   // long rows: rest of the other side
+            const int64_t k = a.mcol[e];
+            if (other && k != j && !(FWD ? (k < j) : (k > j))) acc = fma((double)mv[e], e_old[k], acc);
+        }
+        if (L > 0) {
+            const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
+            const unsigned long long* cnt = done + (int64_t)(L - 1) * SW_SUB;
+            unsigned polls = 0;
+            while (true) {
+                unsigned long long v = ld_acquire_u64(&cnt[lane]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (v >= target) break;
+                if (++polls > (1u << 22)) { ok = false; break; }
+                if (polls > 8) __nanosleep(32);
+            }
+            // each lane acquired one sub-counter; the warp barrier orders every lane's loads
+            // below after all 32 acquires
+            __syncwarp();
+        }
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c)
+            if (kk[c] >= 0) acc = fma(mm[c], e_new[kk[c]], acc);
+        for (int64_t e = e0 + lane + 32 * SW_PF; e < e1; e += 32) {   // long rows: rest of the dependency side
+            const int64_t k = a.mcol[e];
+            if (FWD ? (k < j) : (k > j)) acc = fma((double)mv[e], e_new[k], acc);
+        }
         acc = warp_sum(acc);
-        const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
         if (lane == 0) {
-            if (any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
             const double dj = a.dinv[j];
             const double v = identity ? e_old[j] - acc * dj : (r[j] - acc) * dj;
             e_new[j] = v;
-            st_release_flag(&flags[j], epoch);
+            red_release_add_u64(&done[(int64_t)L * SW_SUB + (gw & (SW_SUB - 1))], 1ull);
         }
         __syncwarp();
     }
+    const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
+    if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
 // rho' = g^T z; first: p = z, else beta = rho'/rho, p = z + beta p; pt = D^{-1} p; epoch++
@@ -245,12 +289,12 @@ __global__ void __launch_bounds__(SP_T) k_sp_gz(SpArgs a) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x)
         t = fma(a.g[j], a.z[j], t);
     t = block_sum(t, sh);
-    if (threadIdx.x == 0) a.part[2 * a.nblk + blockIdx.x] = t;
+    if (threadIdx.x == 0) a.part[a.rblk + a.nblk + blockIdx.x] = t;
 }
 __global__ void __launch_bounds__(SP_T) k_sp_pnext(SpArgs a, int first, int nparts) {
     __shared__ double sh[40];
     if (a.S->done) return;
-    const double rho_new = sum_parts(a.part + 2 * a.nblk, nparts, sh);
+    const double rho_new = sum_parts(a.part + a.rblk + a.nblk, nparts, sh);
     const double beta = first ? 0.0 : rho_new / a.S->rho;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x) {
         const double pj = first ? a.z[j] : fma(beta, a.p[j], a.z[j]);
@@ -308,6 +352,28 @@ __global__ void k_gather_pairs(const float* src, const int64_t* perm, int64_t nn
     }
 }
 
+// Cooperative launch of a sweep with one co-resident grid (every warp must run at once for
+// the level waits to end).
+template <typename MT, bool FWD>
+static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* eold, double* enew,
+                               int identity, int check, int nparts, int idx, cudaStream_t st) {
+    static int grid = 0;
+    auto kern = k_sp_sweep<MT, FWD>;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        LSQ_CUDA(cudaGetDevice(&dev));
+        LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SP_T, 0));
+        if (per < 1) { set_error("sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
+        grid = sms * per;
+    }
+    SpArgs av = a;
+    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &check, &nparts, &idx};
+    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(SP_T), params, 0, st));
+    count_launch();
+    return LSQ_OK;
+}
+
 static unsigned gridn(int64_t work, int64_t cap = 152 * 8) {
     int64_t g = (work + SP_T - 1) / SP_T;
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -321,13 +387,14 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     const int64_t m = A->m, n = A->n, nnz = A->nnz;
     const bool res64 = A->vals_f64 != nullptr || DT == LSQ_F64;
     const size_t es = elem_size(A->dtype);
-    const int nblk = 152 * 4;
+    const int nblk = 152 * 4, rblk = 152 * 16;
     // workspace
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
     size_t o_S = take(sizeof(SpState)), o_vT = take(es * nnz), o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16),
-           o_vec = take(8 * (size_t)n * 10), o_q = take(8 * (size_t)m), o_ff = take(4 * (size_t)n),
-           o_fb = take(4 * (size_t)n), o_part = take(8 * (size_t)nblk * 3), o_n2 = take(64);
+           o_vec = take(8 * (size_t)n * 10), o_q = take(8 * (size_t)m),
+           o_done = take(8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b)), o_part = take(8 * (size_t)(rblk + 2 * nblk)),
+           o_n2 = take(64);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
     char* base = sc.as<char>();
@@ -349,8 +416,12 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.w = vec + 5 * n; a.e0 = vec + 6 * n; a.e1 = vec + 7 * n; a.h = vec + 8 * n;
     double* tmpv = vec + 9 * n;
     a.q = (double*)(base + o_q);
-    a.flag_f = (unsigned*)(base + o_ff); a.flag_b = (unsigned*)(base + o_fb);
-    a.part = (double*)(base + o_part); a.nblk = nblk;
+    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
+    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + SW_SUB * SH->nlev_f;
+    auto lanes_for = [](double mean) { int L = 1; while (L < 32 && L < mean) L <<= 1; return L; };
+    a.lpr = lanes_for((double)nnz / (double)m);
+    a.lpc = lanes_for((double)nnz / (double)n);
+    a.part = (double*)(base + o_part); a.nblk = nblk; a.rblk = rblk;
     a.S = S;
     a.tol = o->tol; a.inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.0; a.maxit = o->maxit;
     double* n2 = (double*)(base + o_n2);
@@ -361,8 +432,8 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     else k_gather_vals<__nv_bfloat16><<<gridn(nnz), SP_T, 0, st>>>(A->vals, SH->atperm, nnz, base + o_vT);
     if (res64 && DT != LSQ_F64) k_gather_vals<double><<<gridn(nnz), SP_T, 0, st>>>(A->vals_f64, SH->atperm, nnz, base + o_vT64);
     count_launch(2);
-    const unsigned grows = gridn((m * 8 + 7) / 8 * 8, nblk), gcols = gridn(n * 32), gvec = gridn(n, nblk);
-    const unsigned gsweep = (unsigned)std::min<int64_t>((n * 32 + SP_T - 1) / SP_T, 152 * 8);
+    // enough lanes in flight for the gathers (the reductions read at most nblk partials)
+    const unsigned grows = gridn(m * a.lpr, rblk), gcols = gridn(n * a.lpc, 152 * 16), gvec = gridn(n, nblk);
     // residual passes read FP64 values when there are FP64 values (the matrix's own or the
     // supplied copy), otherwise the matrix's own dtype
     auto rows = [&](int mode, int use_res, const double* x) {
@@ -374,14 +445,16 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         else k_sp_cols<DT><<<gcols, SP_T, 0, st>>>(a, 0, out);
     };
     // z = P g with t forward and t backward sweeps; epoch advanced per sweep
+    lsq_status sweep_status = LSQ_OK;
     auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int check, int idx) {
-        if (P->op_dtype == LSQ_F32) {
-            if (fwd) k_sp_sweep<float, true><<<gsweep, SP_T, 0, st>>>(a, r, eold, enew, identity, check, gvec, idx);
-            else k_sp_sweep<float, false><<<gsweep, SP_T, 0, st>>>(a, r, eold, enew, identity, check, gvec, idx);
-        } else {
-            if (fwd) k_sp_sweep<double, true><<<gsweep, SP_T, 0, st>>>(a, r, eold, enew, identity, check, gvec, idx);
-            else k_sp_sweep<double, false><<<gsweep, SP_T, 0, st>>>(a, r, eold, enew, identity, check, gvec, idx);
-        }
+        lsq_status q;
+        if (P->op_dtype == LSQ_F32)
+            q = fwd ? launch_sweep<float, true>(a, r, eold, enew, identity, check, gvec, idx, st)
+                    : launch_sweep<float, false>(a, r, eold, enew, identity, check, gvec, idx, st);
+        else
+            q = fwd ? launch_sweep<double, true>(a, r, eold, enew, identity, check, gvec, idx, st)
+                    : launch_sweep<double, false>(a, r, eold, enew, identity, check, gvec, idx, st);
+        if (q != LSQ_OK) sweep_status = q;
     };
     // z = P g: t forward then t backward sweeps (the first may carry the convergence check)
     auto precond = [&](int check) {
@@ -408,8 +481,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     LSQ_CUDA(cudaEventRecord(ev0, st));
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(SpState), st));
-        LSQ_CUDA(cudaMemsetAsync(a.flag_f, 0, 4 * (size_t)n, st));
-        LSQ_CUDA(cudaMemsetAsync(a.flag_b, 0, 4 * (size_t)n, st));
+        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b), st));
         LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)n, st));
         a.b = B ? B + c * ldb : nullptr;
         a.h_in = Hcols ? Hcols + c * ldb : nullptr;
@@ -470,7 +542,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
                 precond(0);
                 k_sp_gz<<<gvec, SP_T, 0, st>>>(a);
                 k_sp_pnext<<<gvec, SP_T, 0, st>>>(a, 1, gvec);
-                count_launch(2 * P->sweeps + 2);
+                count_launch(2);
                 SpState hs{};
                 while (true) {
                     for (int b = 0; b < batch; ++b) {
@@ -481,8 +553,9 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
                         precond(1);
                         k_sp_gz<<<gvec, SP_T, 0, st>>>(a);
                         k_sp_pnext<<<gvec, SP_T, 0, st>>>(a, 0, gvec);
-                        count_launch(2 * P->sweeps + 6);
+                        count_launch(6);
                     }
+                    if (sweep_status != LSQ_OK) return sweep_status;
                     LSQ_CUDA(cudaGetLastError());
                     LSQ_CUDA(cudaMemcpyAsync(&hs, S, sizeof(SpState), cudaMemcpyDeviceToHost, st));
                     LSQ_CUDA(cudaStreamSynchronize(st));
@@ -538,7 +611,8 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     const int64_t n = P->n;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
-    size_t o_S = take(sizeof(SpState)), o_e = take(16 * (size_t)n), o_f = take(8 * (size_t)n);
+    size_t o_S = take(sizeof(SpState)), o_e = take(16 * (size_t)n),
+           o_f = take(8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b));
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
     char* base = sc.as<char>();
@@ -548,32 +622,35 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b; a.sweeps = P->sweeps;
     a.e0 = (double*)(base + o_e); a.e1 = a.e0 + n;
-    a.flag_f = (unsigned*)(base + o_f); a.flag_b = a.flag_f + n;
+    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
+    a.done_f = (unsigned long long*)(base + o_f); a.done_b = a.done_f + SW_SUB * SH->nlev_f;
     a.S = (SpState*)(base + o_S);
-    const unsigned gsweep = (unsigned)std::min<int64_t>((n * 32 + SP_T - 1) / SP_T, 152 * 8);
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(a.S, 0, sizeof(SpState), st));
-        LSQ_CUDA(cudaMemsetAsync(a.flag_f, 0, 8 * (size_t)n, st));
+        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b), st));
         const double* rc = r + c * n;
         double* out = e + c * n;
         const double* eold = nullptr;
         double* bufs[2] = {a.e0, a.e1};
         int cur = 0, idx = 0;
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            if (P->op_dtype == LSQ_F32) k_sp_sweep<float, true><<<gsweep, SP_T, 0, st>>>(a, rc, eold, bufs[cur], 0, 0, 0, idx);
-            else k_sp_sweep<double, true><<<gsweep, SP_T, 0, st>>>(a, rc, eold, bufs[cur], 0, 0, 0, idx);
+            lsq_status q = P->op_dtype == LSQ_F32
+                ? launch_sweep<float, true>(a, rc, eold, bufs[cur], 0, 0, 0, idx, st)
+                : launch_sweep<double, true>(a, rc, eold, bufs[cur], 0, 0, 0, idx, st);
+            if (q != LSQ_OK) return q;
             eold = bufs[cur];
             cur ^= 1;
         }
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
             double* dst = (t == P->sweeps - 1) ? out : bufs[cur];
             const int ident = P->sweeps == 1 ? 1 : 0;
-            if (P->op_dtype == LSQ_F32) k_sp_sweep<float, false><<<gsweep, SP_T, 0, st>>>(a, rc, eold, dst, ident, 0, 0, idx);
-            else k_sp_sweep<double, false><<<gsweep, SP_T, 0, st>>>(a, rc, eold, dst, ident, 0, 0, idx);
+            lsq_status q = P->op_dtype == LSQ_F32
+                ? launch_sweep<float, false>(a, rc, eold, dst, ident, 0, 0, idx, st)
+                : launch_sweep<double, false>(a, rc, eold, dst, ident, 0, 0, idx, st);
+            if (q != LSQ_OK) return q;
             eold = dst;
             cur ^= 1;
         }
-        count_launch(2 * P->sweeps);
     }
     LSQ_CUDA(cudaGetLastError());
     SpState hs{};

@@ -15,6 +15,10 @@ struct SparseHandle {
     // rows listed by forward / backward level (Gauss-Seidel dependency order)
     int32_t* sched_f = nullptr;
     int32_t* sched_b = nullptr;
+    int32_t* lvl_f = nullptr;     // level of each schedule slot
+    int32_t* lvl_b = nullptr;
+    int64_t* lsize_f = nullptr;   // rows per level
+    int64_t* lsize_b = nullptr;
     int64_t nlev_f = 0, nlev_b = 0;
     // transposed pattern of A: column pointers, row indices, source entry of each
     int64_t* atptr = nullptr;

@@ -392,9 +392,14 @@ __global__ void k_to_f32(const double* src, float* dst, int64_t count) {
 
 // Level schedule on the host: lev_f(j) = 1 + max lev_f(k) over k < j with M_jk != 0 (rows in
 // natural order), lev_b(j) = 1 + max lev_b(k) over k > j (rows in reverse order); each
-// schedule lists the rows by level, then by row index.
+// schedule lists the rows by level, then by row index, with the level of every slot and the
+// number of rows of every level.
+struct Levels {
+    std::vector<int32_t> sched, lvl;
+    std::vector<int64_t> size;
+};
 static void host_levels(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                        std::vector<int32_t>& fwd, std::vector<int32_t>& bwd, int64_t* nlev_f, int64_t* nlev_b) {
+                        Levels& F, Levels& B) {
     std::vector<int32_t> lf(n, 0), lb(n, 0);
     int32_t mf = 0, mb = 0;
     for (int64_t j = 0; j < n; ++j) {
@@ -411,17 +416,22 @@ static void host_levels(int64_t n, const std::vector<int64_t>& rp, const std::ve
         lb[j] = l;
         mb = std::max(mb, l);
     }
-    auto order = [n](const std::vector<int32_t>& lev, int32_t maxl, std::vector<int32_t>& out) {
+    auto order = [n](const std::vector<int32_t>& lev, int32_t maxl, Levels& out) {
         std::vector<int64_t> c(maxl + 2, 0);
         for (int64_t j = 0; j < n; ++j) c[lev[j] + 1]++;
+        out.size.assign(maxl + 1, 0);
+        for (int32_t l = 0; l <= maxl; ++l) out.size[l] = c[l + 1];
         for (int32_t l = 0; l <= maxl; ++l) c[l + 1] += c[l];
-        out.assign(n, 0);
-        for (int64_t j = 0; j < n; ++j) out[c[lev[j]]++] = (int32_t)j;
+        out.sched.assign(n, 0);
+        out.lvl.assign(n, 0);
+        for (int64_t j = 0; j < n; ++j) {
+            const int64_t at = c[lev[j]]++;
+            out.sched[at] = (int32_t)j;
+            out.lvl[at] = lev[j];
+        }
     };
-    order(lf, mf, fwd);
-    order(lb, mb, bwd);
-    *nlev_f = mf + 1;
-    *nlev_b = mb + 1;
+    order(lf, mf, F);
+    order(lb, mb, B);
 }
 
 lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p, int64_t s,
@@ -537,12 +547,22 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
     LSQ_CUDA(cudaMemcpyAsync(hrp.data(), S->mptr, 8 * (size_t)(n + 1), cudaMemcpyDeviceToHost, st));
     LSQ_CUDA(cudaMemcpyAsync(hci.data(), S->mcol, 4 * (size_t)mnnz, cudaMemcpyDeviceToHost, st));
     LSQ_CUDA(cudaStreamSynchronize(st));
-    std::vector<int32_t> fwd, bwd;
-    host_levels(n, hrp, hci, fwd, bwd, &S->nlev_f, &S->nlev_b);
+    Levels LF, LB;
+    host_levels(n, hrp, hci, LF, LB);
+    S->nlev_f = (int64_t)LF.size.size();
+    S->nlev_b = (int64_t)LB.size.size();
     LSQ_CUDA(cudaMalloc(&S->sched_f, 4 * (size_t)n));
     LSQ_CUDA(cudaMalloc(&S->sched_b, 4 * (size_t)n));
-    LSQ_CUDA(cudaMemcpyAsync(S->sched_f, fwd.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
-    LSQ_CUDA(cudaMemcpyAsync(S->sched_b, bwd.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    LSQ_CUDA(cudaMalloc(&S->lvl_f, 4 * (size_t)n));
+    LSQ_CUDA(cudaMalloc(&S->lvl_b, 4 * (size_t)n));
+    LSQ_CUDA(cudaMalloc(&S->lsize_f, 8 * (size_t)S->nlev_f));
+    LSQ_CUDA(cudaMalloc(&S->lsize_b, 8 * (size_t)S->nlev_b));
+    LSQ_CUDA(cudaMemcpyAsync(S->sched_f, LF.sched.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    LSQ_CUDA(cudaMemcpyAsync(S->sched_b, LB.sched.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    LSQ_CUDA(cudaMemcpyAsync(S->lvl_f, LF.lvl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    LSQ_CUDA(cudaMemcpyAsync(S->lvl_b, LB.lvl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    LSQ_CUDA(cudaMemcpyAsync(S->lsize_f, LF.size.data(), 8 * (size_t)S->nlev_f, cudaMemcpyHostToDevice, st));
+    LSQ_CUDA(cudaMemcpyAsync(S->lsize_b, LB.size.data(), 8 * (size_t)S->nlev_b, cudaMemcpyHostToDevice, st));
     // 5. transposed pattern of A for the A^T q pass (values are gathered at solve time)
     LSQ_CUDA(cudaMalloc(&S->atptr, 8 * (size_t)(n + 1)));
     LSQ_CUDA(cudaMalloc(&S->atrow, 4 * (size_t)A->nnz));
@@ -563,7 +583,8 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
 void free_sparse(SparseHandle* S) {
     if (!S) return;
     cudaFree(S->mptr); cudaFree(S->mcol); cudaFree(S->mval); cudaFree(S->mval32); cudaFree(S->dinv);
-    cudaFree(S->sched_f); cudaFree(S->sched_b); cudaFree(S->atptr); cudaFree(S->atrow);
+    cudaFree(S->sched_f); cudaFree(S->sched_b); cudaFree(S->lvl_f); cudaFree(S->lvl_b);
+    cudaFree(S->lsize_f); cudaFree(S->lsize_b); cudaFree(S->atptr); cudaFree(S->atrow);
     cudaFree(S->atperm);
     delete S;
 }

@@ -62,9 +62,10 @@ def test_coherent_matrix_draws_identity_rows(lsq, orc):
 
 
 def test_udv_full_size_bitexact(lsq, orc):
-    # the benchmark workload: 262144 x 512 UDV, kappa = 1e6 (QR on the device for speed)
-    qr = lambda G: torch.linalg.qr(torch.from_numpy(G).cuda())[0].cpu().numpy()
-    mat = W.udv_dense(262144, 512, 1e6, 2, qr=qr)
+    # the benchmark workload: 262144 x 512 UDV, kappa = 1e6 (large products on the device)
+    mm = lambda X, Y: (torch.from_numpy(np.ascontiguousarray(X)).cuda()
+                       @ torch.from_numpy(np.ascontiguousarray(Y)).cuda()).cpu().numpy()
+    mat = W.udv_dense(262144, 512, 1e6, 2, matmul=mm)
     _check(lsq, orc, mat, seed=1002)
 
 

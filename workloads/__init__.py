@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "gaussian_dense", "udv_dense", "semi_gaussian_dense", "coherent_dense",
     "sparse_random", "graph_incidence", "rhs_for", "uneven_dense_batch",
-    "csr_from_dense", "dense_from_csr",
+    "csr_from_dense", "dense_from_csr", "orthonormal_q",
 ]
 
 
@@ -39,22 +39,41 @@ def gaussian_dense(m: int, n: int, seed: int) -> dict:
     return {"kind": "dense", "A": np.ascontiguousarray(A)}
 
 
-def udv_dense(m: int, n: int, kappa: float, seed: int, qr=None) -> dict:
+def orthonormal_q(G: np.ndarray, matmul=None) -> np.ndarray:
+    """The Q factor with positive-diagonal R of a tall full-rank G (it is unique), by
+    Cholesky QR applied twice: R = chol(G^T G), Q = G R^{-1}, repeated once on Q.
+
+    ``matmul(X, Y) -> X @ Y`` may run the two large products elsewhere (for example on a
+    device); the n x n Cholesky factors and inverses are computed here in FP64.
+    """
+    mm = matmul or (lambda X, Y: X @ Y)
+    Q = np.asarray(G, dtype=np.float64)
+    R_total = np.eye(Q.shape[1])
+    for _ in range(2):
+        Gram = np.asarray(mm(Q.T, Q))
+        R = np.linalg.cholesky((Gram + Gram.T) / 2).T
+        Rinv = np.linalg.inv(R)
+        Q = np.asarray(mm(Q, Rinv))
+        R_total = R @ R_total
+    return Q
+
+
+def udv_dense(m: int, n: int, kappa: float, seed: int, matmul=None) -> dict:
     """A = U diag(sigma) V^T (Section 5.4, UDV matrix).
 
     U is the orthonormal Q factor of a seeded Gaussian m x n, V the Q factor of a
-    seeded Gaussian n x n, and sigma is log-spaced from 1 down to 1/kappa, so that
-    kappa(A) = kappa.  ``qr`` may be a callable (G -> Q) used for the large QR
-    (for example a device QR); by default numpy's LAPACK QR is used.
+    seeded Gaussian n x n (both with positive-diagonal R), and sigma is log-spaced from 1
+    down to 1/kappa, so that kappa(A) = kappa.  ``matmul`` may run the large products on
+    another device (see orthonormal_q).
     """
     rng = _rng(seed)
     G = rng.standard_normal((m, n))
     H = rng.standard_normal((n, n))
-    qr = qr or (lambda X: np.linalg.qr(X, mode="reduced")[0])
-    U = np.asarray(qr(G), dtype=np.float64)
-    V = np.linalg.qr(H, mode="reduced")[0]
+    U = orthonormal_q(G, matmul)
+    V = orthonormal_q(H)
     sigma = np.logspace(0.0, -math.log10(kappa), n)
-    A = (U * sigma[None, :]) @ V.T
+    mm = matmul or (lambda X, Y: X @ Y)
+    A = np.asarray(mm(U * sigma[None, :], V.T))
     return {"kind": "dense", "A": np.ascontiguousarray(A), "sigma": sigma}
 
 

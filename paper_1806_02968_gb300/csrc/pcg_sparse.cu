@@ -752,6 +752,7 @@ lsq_status sparse_solve(const lsq_matrix* A, const lsq_precond* P, const double*
     LSQ_CHECK_ARG(P->sp != nullptr, "preconditioner was built for a dense matrix");
     LSQ_CHECK_ARG(P->sp->nnz_A == A->nnz && P->sp->m == A->m, "preconditioner was built for another pattern");
     LSQ_CHECK_ARG(P->sweeps <= 32, "sparse sweeps must be <= 32");
+    if (k >= 2) return sparse_block_solve(A, P, B, Hcols, k, ldb, X, ldx, o, info, st);
     switch (A->dtype) {
         case LSQ_F64: return sp_solve_impl<LSQ_F64>(A, P, B, Hcols, k, ldb, X, ldx, o, info, st);
         case LSQ_F32: return sp_solve_impl<LSQ_F32>(A, P, B, Hcols, k, ldb, X, ldx, o, info, st);

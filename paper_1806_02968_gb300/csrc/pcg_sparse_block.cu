@@ -1,0 +1,748 @@
+// Alg. 2 step 4 for a block of K <= 32 right-hand sides of a CSR matrix: K independent PCG
+// recurrences advanced together, so that every pass over A and every Gauss-Seidel sweep
+// over A_s^T A_s serves all K columns.
+//
+// Vectors are stored row-major n x K (element (j, c) at j*K + c); a group of GK lanes
+// (GK = K rounded up to a power of two) handles one row and lane c its column c.  Every
+// column keeps its own alpha, beta, rho and convergence state: a column whose recursive
+// residual meets the tolerance (or that reaches maxit, or breaks down) is frozen (alpha = 0
+// from then on, p and rho no longer updated), so each column follows the iteration it would
+// follow alone; the batch stops when every column is frozen.
+//
+// Per iteration:
+//   k_bk_rows   q = Â p for all columns; the last block sums the partials of p^T w = ||q||^2
+//   k_bk_cols   w = Â^T q
+//   k_bk_update alpha, y += alpha p, g -= alpha w; the last block sums ||g||^2 and freezes
+//               converged columns
+//   k_bk_sweep  t forward and t backward level-ordered Gauss-Seidel sweeps (one level wait
+//               per row for all K columns)
+//   k_bk_gz     rho' = g^T z; the last block forms beta and moves rho on
+//   k_bk_pnext  p = z + beta p, pt = D^{-1} p
+// Reductions are fixed-order (per-block partials, then one block sums them in block order),
+// so results do not depend on timing.
+#include "sparse.cuh"
+#include "values.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace lsq {
+
+constexpr int BK_T = 256;
+constexpr int BK_MAX = 32;
+constexpr int BK_SUB = 32;     // completion sub-counters per level
+constexpr int BK_PF = 8;       // dependency entries per lane loaded before a level wait
+
+struct BkState {
+    double rho[BK_MAX], hn[BK_MAX], gstart[BK_MAX], rec[BK_MAX];
+    double pw[BK_MAX], beta[BK_MAX];
+    int32_t iters[BK_MAX];
+    int32_t active[BK_MAX];    // column still iterating in this inner solve
+    int32_t broke[BK_MAX];     // breakdown (non-positive or non-finite curvature)
+    int32_t done, napply;
+    unsigned err;
+    unsigned arrive[4];        // last-block counters: rows, update, gz, norms
+};
+
+struct BkArgs {
+    int64_t m, n;
+    int K, GK;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const void* vals;
+    const void* vals_res;
+    const int64_t* atptr;
+    const int32_t* atrow;
+    const void* valsT;
+    const void* valsT_res;
+    const double* inv_d;
+    const double* b;          // m x K row-major (least-squares form) or NULL
+    const int64_t* mptr;
+    const int32_t* mcol;
+    const void* mval;
+    const double* dinv;
+    const int32_t* sched_f;
+    const int32_t* sched_b;
+    const int32_t* lvl_f;
+    const int32_t* lvl_b;
+    const int64_t* lsize_f;
+    const int64_t* lsize_b;
+    unsigned long long* done_f;
+    unsigned long long* done_b;
+    int sweeps;
+    double *y, *g, *z, *p, *pt, *w, *q, *e0, *e1, *h;
+    double* part;             // per-block partials, [blocks][K] (x2 for the norms)
+    BkState* S;
+    double tol, inner_tol;
+    int32_t maxit;
+};
+
+__device__ __forceinline__ unsigned long long bk_ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void bk_red_release_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Thread t holds v for column t % GK; out[c] = that column's sum over the block (fixed order).
+__device__ __forceinline__ void bk_block_partials(double v, int K, int GK, double* out, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    if ((int)threadIdx.x < K) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < (int)blockDim.x; i += GK) t += sh[i];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+// After every block has written its partials: true in the one block that arrived last
+// (the partials of all blocks are then visible to it).
+__device__ __forceinline__ bool bk_last_block(unsigned* counter) {
+    __shared__ unsigned s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1) ? 1u : 0u;
+        if (s_last) *counter = 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+// sh[c] = sum over blocks b of part[b*K + c], in a fixed order (a warp per column)
+__device__ __forceinline__ void bk_total(const double* part, int nparts, int K, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = wid; c < K; c += blockDim.x >> 5) {
+        double t = 0.0;
+        for (int b = lane; b < nparts; b += 32) t += __ldcg(part + (int64_t)b * K + c);
+        t = warp_sum(t);
+        if (lane == 0) sh[c] = t;
+    }
+    __syncthreads();
+}
+
+// q_i = A_i x, b_i, or b_i - A_i x (mode 0/1/2) for every column; the last block leaves the
+// column sums of ||q||^2 in S->pw
+template <int DT>
+__global__ void __launch_bounds__(BK_T) k_bk_rows(BkArgs a, int mode, int use_res, const double* x) {
+    __shared__ double sh[BK_T];
+    if (a.S->done) return;
+    const void* vals = use_res ? a.vals_res : a.vals;
+    const int c = threadIdx.x & (a.GK - 1);
+    const bool col_ok = c < a.K;
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    double qq = 0.0;
+    if (col_ok)
+        for (int64_t i = grp; i < a.m; i += ngrp) {
+            double dot = 0.0;
+            if (mode != 1)
+                for (int64_t e = a.row_ptr[i]; e < a.row_ptr[i + 1]; ++e)
+                    dot = fma(Val<DT>::load(vals, e), x[(int64_t)a.col_idx[e] * a.K + c], dot);
+            const double bi = mode == 0 ? 0.0 : a.b[i * a.K + c];
+            const double qv = mode == 0 ? dot : (mode == 1 ? bi : bi - dot);
+            a.q[i * a.K + c] = qv;
+            qq = fma(qv, qv, qq);
+        }
+    bk_block_partials(qq, a.K, a.GK, a.part + (int64_t)blockIdx.x * a.K, sh);
+    if (!bk_last_block(&a.S->arrive[0])) return;
+    bk_total(a.part, gridDim.x, a.K, sh);
+    if ((int)threadIdx.x < a.K) a.S->pw[threadIdx.x] = sh[threadIdx.x];
+}
+
+// out_j = (1/d_j) A^T_j q for every column (the transposed pattern; no atomics)
+template <int DT>
+__global__ void __launch_bounds__(BK_T) k_bk_cols(BkArgs a, int use_res, double* out) {
+    if (a.S->done) return;
+    const void* vals = use_res ? a.valsT_res : a.valsT;
+    const int c = threadIdx.x & (a.GK - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    if (c >= a.K) return;
+    for (int64_t j = grp; j < a.n; j += ngrp) {
+        double t = 0.0;
+        for (int64_t e = a.atptr[j]; e < a.atptr[j + 1]; ++e)
+            t = fma(Val<DT>::load(vals, e), a.q[(int64_t)a.atrow[e] * a.K + c], t);
+        out[j * a.K + c] = t * a.inv_d[j];
+    }
+}
+
+// alpha_c = rho_c / p_c^T w_c (0 for frozen columns), y += alpha p, g -= alpha w.  The last
+// block sums ||g||^2, counts the iteration of every active column and freezes the columns
+// that met the tolerance or maxit; S->done once none is left.
+__global__ void __launch_bounds__(BK_T) k_bk_update(BkArgs a) {
+    __shared__ double sh[BK_T];
+    __shared__ double s_alpha[BK_MAX];
+    __shared__ int s_any;
+    if (a.S->done) return;
+    if ((int)threadIdx.x < a.K) {
+        const int c = threadIdx.x;
+        const double pw = a.S->pw[c], rho = a.S->rho[c];
+        const bool ok = pw > 0.0 && rho > 0.0 && isfinite(pw) && isfinite(rho);
+        s_alpha[c] = (a.S->active[c] && ok) ? rho / pw : 0.0;
+    }
+    __syncthreads();
+    const int c = threadIdx.x & (a.GK - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    double gg = 0.0;
+    if (c < a.K) {
+        const double al = s_alpha[c];
+        for (int64_t j = grp; j < a.n; j += ngrp) {
+            const int64_t at = j * a.K + c;
+            a.y[at] = fma(al, a.p[at], a.y[at]);
+            const double gj = fma(-al, a.w[at], a.g[at]);
+            a.g[at] = gj;
+            gg = fma(gj, gj, gg);
+        }
+    }
+    bk_block_partials(gg, a.K, a.GK, a.part + (int64_t)blockIdx.x * a.K, sh);
+    if (!bk_last_block(&a.S->arrive[1])) return;
+    bk_total(a.part, gridDim.x, a.K, sh);
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    if ((int)threadIdx.x < a.K) {
+        const int cc = threadIdx.x;
+        if (a.S->active[cc]) {
+            const double pw = a.S->pw[cc], rho = a.S->rho[cc];
+            if (!(pw > 0.0 && rho > 0.0 && isfinite(pw) && isfinite(rho))) {
+                a.S->broke[cc] = 1;
+                a.S->active[cc] = 0;
+            } else {
+                a.S->iters[cc] += 1;
+                const double gn = sqrt(sh[cc]);
+                a.S->rec[cc] = gn / a.S->hn[cc];
+                if (gn <= a.tol * a.S->hn[cc] || gn <= a.inner_tol * a.S->gstart[cc] || a.S->iters[cc] >= a.maxit)
+                    a.S->active[cc] = 0;
+            }
+        }
+        if (a.S->active[cc]) atomicOr(&s_any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !s_any) a.S->done = 1;
+}
+
+// One Gauss-Seidel sweep of Alg. 3 for all K columns, level-ordered without grid barriers
+// (cooperative launch; warp w takes schedule slots w, w + W, ...; a row of level L waits on
+// the 32 completion sub-counters of level L-1, bounded polls).  A warp takes a row; the
+// row's entries are loaded 32 at a time and broadcast by shuffles; lane c accumulates
+// column c.  `identity`: the backward sweep right after one forward sweep from zero.
+template <typename MT, bool FWD>
+__global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, const double* e_old,
+                                                   double* e_new, int identity, int sweep_idx) {
+    if (a.S->done) return;
+    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
+    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
+    unsigned long long* done = FWD ? a.done_f : a.done_b;
+    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
+    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
+    const int32_t* sched = FWD ? a.sched_f : a.sched_b;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const int lane = threadIdx.x & 31;
+    const int K = a.K;
+    const bool col_ok = lane < K;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool other = !identity && e_old != nullptr;
+    bool ok = true;
+    for (int64_t slot = gw; slot < a.n; slot += W) {
+        const int64_t j = sched[slot];
+        const int L = lvl[slot];
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1];
+        double acc = 0.0;
+        if (other) {   // previous sweep's values on the other side: no wait needed
+            for (int64_t base = e0; base < e1; base += 32) {
+                const int64_t e = base + lane;
+                int32_t kk = -1;
+                double mm = 0.0;
+                if (e < e1) { kk = a.mcol[e]; mm = (double)mv[e]; }
+                const int cnt = (int)min((int64_t)32, e1 - base);
+                for (int t = 0; t < cnt; ++t) {
+                    const int32_t k = __shfl_sync(0xffffffffu, kk, t);
+                    const double mk = __shfl_sync(0xffffffffu, mm, t);
+                    if ((FWD ? (k > j) : (k < j)) && col_ok) acc = fma(mk, e_old[(int64_t)k * K + lane], acc);
+                }
+            }
+        }
+        int32_t pk[BK_PF];
+        double pm[BK_PF];
+#pragma unroll
+        for (int c = 0; c < BK_PF; ++c) {
+            const int64_t e = e0 + lane + 32 * c;
+            pk[c] = -1;
+            pm[c] = 0.0;
+            if (e < e1) { pk[c] = a.mcol[e]; pm[c] = (double)mv[e]; }
+        }
+        if (L > 0) {
+            const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
+            const unsigned long long* cntp = done + (int64_t)(L - 1) * BK_SUB;
+            unsigned polls = 0;
+            while (true) {
+                unsigned long long v = bk_ld_acquire_u64(&cntp[lane]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (v >= target) break;
+                if (++polls > (1u << 22)) { ok = false; break; }
+                if (polls > 8) __nanosleep(32);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int c = 0; c < BK_PF; ++c) {
+            const int64_t cbase = e0 + 32 * c;
+            if (cbase < e1) {
+                const int cnt = (int)min((int64_t)32, e1 - cbase);
+                for (int t = 0; t < cnt; ++t) {
+                    const int32_t k = __shfl_sync(0xffffffffu, pk[c], t);
+                    const double mk = __shfl_sync(0xffffffffu, pm[c], t);
+                    if ((FWD ? (k < j) : (k > j)) && col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
+                }
+            }
+        }
+        for (int64_t base = e0 + 32 * BK_PF; base < e1; base += 32) {   // long rows
+            const int64_t e = base + lane;
+            int32_t kk = -1;
+            double mm = 0.0;
+            if (e < e1) { kk = a.mcol[e]; mm = (double)mv[e]; }
+            const int cnt = (int)min((int64_t)32, e1 - base);
+            for (int t = 0; t < cnt; ++t) {
+                const int32_t k = __shfl_sync(0xffffffffu, kk, t);
+                const double mk = __shfl_sync(0xffffffffu, mm, t);
+                if ((FWD ? (k < j) : (k > j)) && col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
+            }
+        }
+        if (col_ok) {
+            const double dj = a.dinv[j];
+            const int64_t at = j * K + lane;
+            e_new[at] = identity ? e_old[at] - acc * dj : (r[at] - acc) * dj;
+        }
+        __syncwarp();
+        if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * BK_SUB + (gw & (BK_SUB - 1))], 1ull);
+    }
+    const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
+    if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+}
+
+// rho'_c = g_c^T z_c; the last block sets beta_c = rho'_c / rho_c (0 on the first call) and
+// rho_c = rho'_c for the active columns, and counts the preconditioner application
+__global__ void __launch_bounds__(BK_T) k_bk_gz(BkArgs a, int first) {
+    __shared__ double sh[BK_T];
+    if (a.S->done) return;
+    const int c = threadIdx.x & (a.GK - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    double t = 0.0;
+    if (c < a.K)
+        for (int64_t j = grp; j < a.n; j += ngrp) t = fma(a.g[j * a.K + c], a.z[j * a.K + c], t);
+    bk_block_partials(t, a.K, a.GK, a.part + (int64_t)blockIdx.x * a.K, sh);
+    if (!bk_last_block(&a.S->arrive[2])) return;
+    bk_total(a.part, gridDim.x, a.K, sh);
+    if ((int)threadIdx.x < a.K) {
+        const int cc = threadIdx.x;
+        if (a.S->active[cc]) {
+            a.S->beta[cc] = first ? 0.0 : sh[cc] / a.S->rho[cc];
+            a.S->rho[cc] = sh[cc];
+        }
+    }
+    if (threadIdx.x == 0) a.S->napply += 1;
+}
+// p = z + beta p (p = z first), pt = D^{-1} p, for the active columns
+__global__ void __launch_bounds__(BK_T) k_bk_pnext(BkArgs a) {
+    if (a.S->done) return;
+    const int c = threadIdx.x & (a.GK - 1);
+    if (c >= a.K || !a.S->active[c]) return;
+    const double be = a.S->beta[c];
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    for (int64_t j = grp; j < a.n; j += ngrp) {
+        const int64_t at = j * a.K + c;
+        const double pj = fma(be, a.p[at], a.z[at]);
+        a.p[at] = pj;
+        a.pt[at] = pj * a.inv_d[j];
+    }
+}
+// out2[c] = ||x_c||^2, out2[BK_MAX + c] = ||D x_c||^2 (runs whatever S->done says)
+__global__ void __launch_bounds__(BK_T) k_bk_norms(BkArgs a, const double* x, double* out2) {
+    __shared__ double sh[BK_T];
+    const int c = threadIdx.x & (a.GK - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    double t = 0.0, r = 0.0;
+    if (c < a.K)
+        for (int64_t j = grp; j < a.n; j += ngrp) {
+            const double v = x[j * a.K + c], vr = v / a.inv_d[j];
+            t = fma(v, v, t);
+            r = fma(vr, vr, r);
+        }
+    double* part2 = a.part + (int64_t)gridDim.x * a.K;
+    bk_block_partials(t, a.K, a.GK, a.part + (int64_t)blockIdx.x * a.K, sh);
+    bk_block_partials(r, a.K, a.GK, part2 + (int64_t)blockIdx.x * a.K, sh);
+    if (!bk_last_block(&a.S->arrive[3])) return;
+    bk_total(a.part, gridDim.x, a.K, sh);
+    if ((int)threadIdx.x < a.K) out2[threadIdx.x] = sh[threadIdx.x];
+    __syncthreads();
+    bk_total(part2, gridDim.x, a.K, sh);
+    if ((int)threadIdx.x < a.K) out2[BK_MAX + threadIdx.x] = sh[threadIdx.x];
+}
+// column-major (leading dimension ld) -> row-major n x K
+__global__ void k_bk_to_rows(const double* src, int64_t ld, int64_t n, int K, double* dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * K; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / K, c = t % K;
+        dst[t] = src[c * ld + j];
+    }
+}
+// row-major n x K scaled by s_j -> column-major (leading dimension ld)
+__global__ void k_bk_from_rows(const double* src, int64_t n, int K, const double* s, double* dst, int64_t ld) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * K; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t / n, j = t % n;
+        dst[c * ld + j] = src[j * K + c] * s[j];
+    }
+}
+__global__ void k_bk_diff(const double* h, const double* w, double* g, int64_t cnt) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        g[t] = h[t] - w[t];
+}
+__global__ void k_bk_scale(const double* src, int64_t n, int K, const double* s, double* dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * K; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = src[t] * s[t / K];
+}
+template <typename T>
+__global__ void k_bk_gather(const void* src, const int64_t* perm, int64_t nnz, void* dst) {
+    const T* s = reinterpret_cast<const T*>(src);
+    T* d = reinterpret_cast<T*>(dst);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        d[e] = s[perm[e]];
+}
+__global__ void k_bk_gather_pairs(const float* src, const int64_t* perm, int64_t nnz, float* dst) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        dst[2 * e] = src[2 * perm[e]];
+        dst[2 * e + 1] = src[2 * perm[e] + 1];
+    }
+}
+
+static unsigned bk_grid(int64_t work, int64_t cap) {
+    int64_t g = (work + BK_T - 1) / BK_T;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// Cooperative launch: every warp of the sweep must be resident for the level waits to end.
+template <typename MT, bool FWD>
+static lsq_status bk_launch_sweep(const BkArgs& a, const double* r, const double* eold, double* enew,
+                                  int identity, int idx, cudaStream_t st) {
+    static int grid = 0;
+    auto kern = k_bk_sweep<MT, FWD>;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        LSQ_CUDA(cudaGetDevice(&dev));
+        LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BK_T, 0));
+        if (per < 1) { set_error("block sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
+        grid = sms * per;
+    }
+    BkArgs av = a;
+    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &idx};
+    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(BK_T), params, 0, st));
+    count_launch();
+    return LSQ_OK;
+}
+
+struct BkOut {
+    int32_t iters[BK_MAX], outer[BK_MAX];
+    uint8_t conv[BK_MAX];
+    double rec[BK_MAX], tru[BK_MAX], raw[BK_MAX];
+    lsq_status status[BK_MAX];
+};
+
+// One block of K columns: B (m x K) or Hcols (n x K) column-major with leading dimension ldb,
+// X column-major with leading dimension ldx.
+template <int DT>
+static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const double* B, const double* Hcols,
+                                int K, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o, BkOut* out,
+                                cudaStream_t st) {
+    const SparseHandle* SH = P->sp;
+    const int64_t m = A->m, n = A->n, nnz = A->nnz;
+    const bool res64 = A->vals_f64 != nullptr || DT == LSQ_F64;
+    const size_t es = elem_size(A->dtype);
+    const int64_t grid_cap = 152 * 16;
+    int GK = 1;
+    while (GK < K) GK <<= 1;
+    const int64_t nK = n * K;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
+    const size_t o_S = take(sizeof(BkState)), o_vT = take(es * nnz),
+                 o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16), o_vec = take(8 * (size_t)nK * 10),
+                 o_q = take(8 * (size_t)m * K), o_b = take(B ? 8 * (size_t)m * K : 16),
+                 o_done = take(8 * (size_t)BK_SUB * (SH->nlev_f + SH->nlev_b)),
+                 o_part = take(8 * (size_t)2 * grid_cap * K), o_n2 = take(8 * 2 * BK_MAX);
+    Scratch sc;
+    LSQ_CUDA(sc.alloc(off, st));
+    char* base = sc.as<char>();
+    BkState* S = (BkState*)(base + o_S);
+    double* vec = (double*)(base + o_vec);
+    BkArgs a{};
+    a.m = m; a.n = n; a.K = K; a.GK = GK;
+    a.row_ptr = A->row_ptr; a.col_idx = A->col_idx; a.vals = A->vals;
+    a.vals_res = res64 ? (DT == LSQ_F64 ? A->vals : (const void*)A->vals_f64) : A->vals;
+    a.atptr = SH->atptr; a.atrow = SH->atrow;
+    a.valsT = base + o_vT;
+    a.valsT_res = res64 ? (DT == LSQ_F64 ? a.valsT : (const void*)(base + o_vT64)) : a.valsT;
+    a.inv_d = P->inv_d;
+    a.b = B ? (const double*)(base + o_b) : nullptr;
+    a.mptr = SH->mptr; a.mcol = SH->mcol;
+    a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
+    a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
+    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
+    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + BK_SUB * SH->nlev_f;
+    a.sweeps = P->sweeps;
+    a.y = vec; a.g = vec + nK; a.z = vec + 2 * nK; a.p = vec + 3 * nK; a.pt = vec + 4 * nK;
+    a.w = vec + 5 * nK; a.e0 = vec + 6 * nK; a.e1 = vec + 7 * nK; a.h = vec + 8 * nK;
+    double* tmpv = vec + 9 * nK;
+    a.q = (double*)(base + o_q);
+    a.part = (double*)(base + o_part);
+    a.S = S;
+    a.tol = o->tol; a.inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.0; a.maxit = o->maxit;
+    double* n2 = (double*)(base + o_n2);
+    // A^T values in column order; the right-hand sides row-major
+    if (DT == LSQ_F32X2) k_bk_gather_pairs<<<bk_grid(nnz, 4096), BK_T, 0, st>>>((const float*)A->vals, SH->atperm, nnz, (float*)(base + o_vT));
+    else if (es == 8) k_bk_gather<double><<<bk_grid(nnz, 4096), BK_T, 0, st>>>(A->vals, SH->atperm, nnz, base + o_vT);
+    else if (es == 4) k_bk_gather<float><<<bk_grid(nnz, 4096), BK_T, 0, st>>>(A->vals, SH->atperm, nnz, base + o_vT);
+    else k_bk_gather<__nv_bfloat16><<<bk_grid(nnz, 4096), BK_T, 0, st>>>(A->vals, SH->atperm, nnz, base + o_vT);
+    count_launch();
+    if (res64 && DT != LSQ_F64) {
+        k_bk_gather<double><<<bk_grid(nnz, 4096), BK_T, 0, st>>>(A->vals_f64, SH->atperm, nnz, base + o_vT64);
+        count_launch();
+    }
+    if (B) {
+        k_bk_to_rows<<<bk_grid(m * K, 4096), BK_T, 0, st>>>(B, ldb, m, K, (double*)(base + o_b));
+        count_launch();
+    }
+    const unsigned grows = bk_grid(m * GK, grid_cap), gcols = bk_grid(n * GK, grid_cap), gvec = bk_grid(n * GK, 152 * 4);
+    auto rows = [&](int mode, int use_res, const double* x) {
+        if (use_res && res64) k_bk_rows<LSQ_F64><<<grows, BK_T, 0, st>>>(a, mode, 1, x);
+        else k_bk_rows<DT><<<grows, BK_T, 0, st>>>(a, mode, 0, x);
+        count_launch();
+    };
+    auto cols = [&](int use_res, double* dst) {
+        if (use_res && res64) k_bk_cols<LSQ_F64><<<gcols, BK_T, 0, st>>>(a, 1, dst);
+        else k_bk_cols<DT><<<gcols, BK_T, 0, st>>>(a, 0, dst);
+        count_launch();
+    };
+    lsq_status sweep_status = LSQ_OK;
+    auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int idx) {
+        lsq_status q;
+        if (P->op_dtype == LSQ_F32)
+            q = fwd ? bk_launch_sweep<float, true>(a, r, eold, enew, identity, idx, st)
+                    : bk_launch_sweep<float, false>(a, r, eold, enew, identity, idx, st);
+        else
+            q = fwd ? bk_launch_sweep<double, true>(a, r, eold, enew, identity, idx, st)
+                    : bk_launch_sweep<double, false>(a, r, eold, enew, identity, idx, st);
+        if (q != LSQ_OK) sweep_status = q;
+    };
+    // z = P g: t forward then t backward sweeps
+    auto precond = [&]() {
+        const double* eold = nullptr;
+        double* bufs[2] = {a.e0, a.e1};
+        int cur = 0, idx = 0;
+        for (int t = 0; t < P->sweeps; ++t, ++idx) {
+            sweep(true, a.g, eold, bufs[cur], 0, idx);
+            eold = bufs[cur];
+            cur ^= 1;
+        }
+        for (int t = 0; t < P->sweeps; ++t, ++idx) {
+            double* dst = (t == P->sweeps - 1) ? a.z : bufs[cur];
+            sweep(false, a.g, eold, dst, (P->sweeps == 1) ? 1 : 0, idx);
+            eold = dst;
+            cur ^= 1;
+        }
+    };
+    double gn[BK_MAX], gn_raw[BK_MAX];
+    auto norms = [&](const double* x) -> lsq_status {
+        k_bk_norms<<<gvec, BK_T, 0, st>>>(a, x, n2);
+        count_launch();
+        double hb[2 * BK_MAX];
+        LSQ_CUDA(cudaMemcpyAsync(hb, n2, sizeof(hb), cudaMemcpyDeviceToHost, st));
+        LSQ_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < K; ++c) { gn[c] = std::sqrt(hb[c]); gn_raw[c] = std::sqrt(hb[BK_MAX + c]); }
+        return LSQ_OK;
+    };
+    LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(BkState), st));
+    LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)BK_SUB * (SH->nlev_f + SH->nlev_b), st));
+    LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)nK, st));
+    if (Hcols) {
+        k_bk_to_rows<<<bk_grid(nK, 4096), BK_T, 0, st>>>(Hcols, ldb, n, K, a.h);
+        count_launch();
+    } else {
+        rows(1, 1, a.pt);
+        cols(1, a.h);
+    }
+    LSQ_CUDA(cudaMemcpyAsync(a.g, a.h, 8 * (size_t)nK, cudaMemcpyDeviceToDevice, st));
+    lsq_status r0 = norms(a.h);
+    if (r0 != LSQ_OK) return r0;
+    double hn[BK_MAX], hn_raw[BK_MAX];
+    for (int c = 0; c < K; ++c) { hn[c] = gn[c]; hn_raw[c] = gn_raw[c]; }
+    int iters[BK_MAX] = {}, outer_used[BK_MAX] = {}, conv[BK_MAX] = {}, broke[BK_MAX] = {};
+    bool dirty[BK_MAX] = {};
+    double rec[BK_MAX], tru[BK_MAX], raw[BK_MAX];
+    int napply = 0;
+    auto true_residual = [&]() -> lsq_status {
+        LSQ_CUDA(cudaMemsetAsync(&S->done, 0, sizeof(int32_t), st));
+        k_bk_scale<<<bk_grid(nK, 4096), BK_T, 0, st>>>(a.y, n, K, a.inv_d, tmpv);
+        count_launch();
+        if (Hcols) {
+            rows(0, 1, tmpv);
+            cols(1, a.w);
+            k_bk_diff<<<bk_grid(nK, 4096), BK_T, 0, st>>>(a.h, a.w, a.g, nK);
+            count_launch();
+        } else {
+            rows(2, 1, tmpv);
+            cols(1, a.g);
+        }
+        for (int c = 0; c < K; ++c) dirty[c] = false;
+        return norms(a.g);
+    };
+    for (int c = 0; c < K; ++c) {
+        rec[c] = tru[c] = raw[c] = 1.0;
+        if (hn[c] == 0.0) { conv[c] = 1; rec[c] = tru[c] = raw[c] = 0.0; }
+    }
+    for (int outer = 0; outer < o->max_outer; ++outer) {
+        if (outer > 0) {
+            lsq_status rs = true_residual();
+            if (rs != LSQ_OK) return rs;
+        }
+        BkState init{};
+        int nact = 0;
+        for (int c = 0; c < K; ++c) {
+            init.hn[c] = hn[c] > 0.0 ? hn[c] : 1.0;
+            if (hn[c] == 0.0 || broke[c]) continue;
+            tru[c] = gn[c] / hn[c];
+            raw[c] = hn_raw[c] > 0.0 ? gn_raw[c] / hn_raw[c] : 0.0;
+            if (outer == 0) rec[c] = tru[c];
+            if (tru[c] <= o->tol) { conv[c] = 1; continue; }
+            if (iters[c] >= o->maxit) continue;
+            init.active[c] = 1;
+            init.gstart[c] = gn[c];
+            outer_used[c] = outer + 1;
+            ++nact;
+        }
+        if (nact == 0) break;
+        for (int c = 0; c < K; ++c) { init.iters[c] = iters[c]; init.rec[c] = rec[c]; }
+        init.napply = napply;
+        LSQ_CUDA(cudaMemcpyAsync(S, &init, sizeof(BkState), cudaMemcpyHostToDevice, st));
+        // z = P g, rho = g^T z, p = z
+        precond();
+        k_bk_gz<<<gvec, BK_T, 0, st>>>(a, 1);
+        k_bk_pnext<<<gvec, BK_T, 0, st>>>(a);
+        count_launch(2);
+        BkState hs{};
+        while (true) {
+            for (int b = 0; b < 8; ++b) {
+                rows(0, 0, a.pt);
+                cols(0, a.w);
+                k_bk_update<<<gvec, BK_T, 0, st>>>(a);
+                precond();
+                k_bk_gz<<<gvec, BK_T, 0, st>>>(a, 0);
+                k_bk_pnext<<<gvec, BK_T, 0, st>>>(a);
+                count_launch(3);
+            }
+            if (sweep_status != LSQ_OK) return sweep_status;
+            LSQ_CUDA(cudaGetLastError());
+            LSQ_CUDA(cudaMemcpyAsync(&hs, S, sizeof(BkState), cudaMemcpyDeviceToHost, st));
+            LSQ_CUDA(cudaStreamSynchronize(st));
+            if (hs.err) { set_error("block Gauss-Seidel sweep: a level wait timed out"); return LSQ_ERR_TIMEOUT; }
+            if (hs.done) break;
+        }
+        for (int c = 0; c < K; ++c) {
+            if (!init.active[c]) continue;
+            if (hs.iters[c] > iters[c]) dirty[c] = true;
+            iters[c] = hs.iters[c];
+            rec[c] = hs.rec[c];
+            if (hs.broke[c]) broke[c] = 1;
+        }
+        napply = hs.napply;
+    }
+    bool was[BK_MAX];
+    bool any_dirty = false;
+    for (int c = 0; c < K; ++c) {
+        was[c] = dirty[c] && !broke[c] && !conv[c];
+        any_dirty = any_dirty || was[c];
+    }
+    if (any_dirty) {
+        lsq_status rs = true_residual();
+        if (rs != LSQ_OK) return rs;
+        for (int c = 0; c < K; ++c) {
+            if (!was[c]) continue;
+            tru[c] = gn[c] / hn[c];
+            raw[c] = hn_raw[c] > 0.0 ? gn_raw[c] / hn_raw[c] : 0.0;
+            if (tru[c] <= o->tol) conv[c] = 1;
+        }
+    }
+    k_bk_from_rows<<<bk_grid(nK, 4096), BK_T, 0, st>>>(a.y, n, K, a.inv_d, X, ldx);
+    count_launch();
+    LSQ_CUDA(cudaGetLastError());
+    LSQ_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < K; ++c) {
+        out->iters[c] = iters[c]; out->outer[c] = outer_used[c]; out->conv[c] = (uint8_t)conv[c];
+        out->rec[c] = rec[c]; out->tru[c] = tru[c]; out->raw[c] = raw[c];
+        out->status[c] = conv[c] ? LSQ_OK : (broke[c] ? LSQ_ERR_BREAKDOWN : LSQ_ERR_NOT_CONVERGED);
+    }
+    return LSQ_OK;
+}
+
+lsq_status sparse_block_solve(const lsq_matrix* A, const lsq_precond* P, const double* B, const double* Hcols,
+                              int64_t k, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o, lsq_info* info,
+                              cudaStream_t st) {
+    LSQ_CHECK_ARG(P->sp != nullptr, "preconditioner was built for a dense matrix");
+    LSQ_CHECK_ARG(P->sp->nnz_A == A->nnz && P->sp->m == A->m, "preconditioner was built for another pattern");
+    LSQ_CHECK_ARG(P->sweeps <= 32, "sparse sweeps must be <= 32");
+    cudaEvent_t ev0, ev1;
+    LSQ_CUDA(cudaEventCreate(&ev0));
+    LSQ_CUDA(cudaEventCreate(&ev1));
+    LSQ_CUDA(cudaEventRecord(ev0, st));
+    lsq_status worst = LSQ_OK;
+    for (int64_t c0 = 0; c0 < k; c0 += BK_MAX) {
+        const int K = (int)std::min<int64_t>(BK_MAX, k - c0);
+        BkOut bo{};
+        const double* Bc = B ? B + c0 * ldb : nullptr;
+        const double* Hc = Hcols ? Hcols + c0 * ldb : nullptr;
+        double* Xc = X + c0 * ldx;
+        lsq_status r;
+        switch (A->dtype) {
+            case LSQ_F64: r = bk_solve_impl<LSQ_F64>(A, P, Bc, Hc, K, ldb, Xc, ldx, o, &bo, st); break;
+            case LSQ_F32: r = bk_solve_impl<LSQ_F32>(A, P, Bc, Hc, K, ldb, Xc, ldx, o, &bo, st); break;
+            case LSQ_BF16: r = bk_solve_impl<LSQ_BF16>(A, P, Bc, Hc, K, ldb, Xc, ldx, o, &bo, st); break;
+            default: r = bk_solve_impl<LSQ_F32X2>(A, P, Bc, Hc, K, ldb, Xc, ldx, o, &bo, st); break;
+        }
+        if (r != LSQ_OK) return r;
+        for (int c = 0; c < K; ++c) {
+            const int64_t at = c0 + c;
+            if (info && at < info->k) {
+                if (info->iters) info->iters[at] = bo.iters[c];
+                if (info->outer) info->outer[at] = bo.outer[c];
+                if (info->converged) info->converged[at] = bo.conv[c];
+                if (info->relres_rec) info->relres_rec[at] = bo.rec[c];
+                if (info->relres_true) info->relres_true[at] = bo.tru[c];
+                if (info->relres_raw) info->relres_raw[at] = bo.raw[c];
+            }
+            if (bo.status[c] == LSQ_ERR_BREAKDOWN) worst = LSQ_ERR_BREAKDOWN;
+            else if (bo.status[c] != LSQ_OK && worst == LSQ_OK) worst = bo.status[c];
+        }
+    }
+    LSQ_CUDA(cudaEventRecord(ev1, st));
+    LSQ_CUDA(cudaEventSynchronize(ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (info) {
+        info->s = P->s; info->nnz_M = P->nnz_M; info->n_fixed_diag = P->n_fixed_diag;
+        info->levels = P->levels; info->solve_ms = ms;
+    }
+    if (worst == LSQ_ERR_NOT_CONVERGED) set_error("PCG did not reach the tolerance");
+    if (worst == LSQ_ERR_BREAKDOWN) set_error("PCG breakdown (non-positive or non-finite curvature)");
+    return worst;
+}
+
+}  // namespace lsq

@@ -35,6 +35,10 @@ void free_sparse(SparseHandle* S);
 lsq_status sparse_solve(const lsq_matrix* A, const lsq_precond* P, const double* B, const double* Hcols,
                         int64_t k, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o, lsq_info* info,
                         cudaStream_t st);
+// k >= 2 right-hand sides: blocks of up to 32 columns advanced together (pcg_sparse_block.cu)
+lsq_status sparse_block_solve(const lsq_matrix* A, const lsq_precond* P, const double* B, const double* Hcols,
+                              int64_t k, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o, lsq_info* info,
+                              cudaStream_t st);
 lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_t k, cudaStream_t st);
 lsq_status sparse_adjoint(const lsq_matrix* A, const lsq_precond* P, const double* X, const double* B,
                           const double* G, int64_t k, int64_t ldb, int64_t ldx, double* grad_b,

@@ -91,3 +91,79 @@ def test_sparse_adjoint_matches_oracle(lsq, orc):
         assert rel(gb[c].cpu().numpy(), gbr) <= 1e-8
         gsum = gsum + gvr
     assert rel(gv.cpu().numpy(), gsum) <= 1e-8
+
+
+@pytest.mark.parametrize("case", ["sprand", "graph"])
+def test_sparse_pcg_single_column_matches_oracle(lsq, orc, case):
+    """k = 1 runs the one-column path (lanes per row of A; scalar recurrences)."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 2029)
+    xs, b = W.rhs_for(seen, 1, 1e-3, 23)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
+    A = W.dense_from_csr(seen)
+    kappa = np.linalg.cond(A / smp.d)
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+    assert info.converged[0] == 1 and oi["converged"] == 1
+    assert rel(X.cpu().numpy().reshape(-1), y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+    assert abs(int(info.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
+
+
+def test_sparse_block_ragged_mixed_columns(lsq, orc):
+    """37 right-hand sides = a block of 32 and a ragged block of 5; one zero column, one
+    consistent column (b in the range of A), the rest noisy.  Every column must match the
+    same column solved alone (one-column path) and, for a few, the oracle."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["sprand"](), 41)
+    k = 37
+    xs, b = W.rhs_for(seen, k, 1e-3, 5)
+    b[3] = 0.0
+    A = W.dense_from_csr(seen)
+    b[6] = A @ xs[6]
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    kappa = np.linalg.cond(A / smp.d)
+    bound = max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+    assert np.all(X[3] == 0.0) and info.iters[3] == 0 and info.converged[3] == 1
+    assert rel(X[6], xs[6]) <= bound
+    for c in range(k):
+        assert info.converged[c] == 1 and info.relres_true[c] <= o.tol, c
+    for c in [0, 6, 31, 32, 36]:
+        x1, i1 = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[c]).cuda(), o)
+        assert rel(X[c], x1.cpu().numpy().reshape(-1)) <= bound, c
+        assert abs(int(info.iters[c]) - int(i1.iters[0])) <= 2, (c, info.iters[c], i1.iters[0])
+    for c in [0, 36]:
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+        assert rel(X[c], y / smp.d) <= bound
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
+
+
+def test_sparse_block_maxit_and_two_sweeps(lsq, orc):
+    """t = 2 sweeps per direction in the block path; a maxit cap freezes every column at
+    exactly maxit iterations, reported as not converged."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["graph"](), 77, sweeps=2)
+    xs, b = W.rhs_for(seen, 3, 1e-4, 12)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    A = W.dense_from_csr(seen)
+    kappa = np.linalg.cond(A / smp.d)
+    for c in range(3):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=2)
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
+    o.maxit = 3
+    o.max_outer = 1
+    X3, i3 = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    assert list(i3.iters) == [3, 3, 3] and not any(i3.converged)
+    for c in range(3):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=3, max_outer=1, sweeps=2)
+        assert oi["iters"] == 3
+        assert rel(X3[c].cpu().numpy(), y / smp.d) <= 1e-10
+
+
+def test_sparse_block_f32_refinement(lsq, orc):
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["sprand"](), 8, dtype="f32", pdt=1, with_f64=True)
+    o.max_outer = 30
+    o.inner_tol = 1e-4
+    xs, b = W.rhs_for(seen, 4, 1e-3, 19)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    for c in range(4):
+        assert info.converged[c] == 1 and info.relres_true[c] <= o.tol

@@ -7,11 +7,10 @@
 //   k_sp_update alpha = rho / p^T w, y += alpha p, g -= alpha w, partials of ||g||^2
 //   k_sp_sweep  forward then backward Gauss-Seidel sweep (the first checks convergence)
 //   k_sp_pnext  rho' = g^T z, beta, p = z + beta p
-// The sweeps keep the natural row order of Alg. 3: each row waits for the rows it depends
-// on (its lower, resp. upper, entries).  Warps take rows in level order from a ticket
-// counter, so a row's dependencies are always held by running or finished warps; the
-// waits on the per-row completion flags are bounded.  A device flag ends the remaining
-// kernels of a batch once PCG has converged.
+// The sweeps keep the natural row order of Alg. 3: a row depends on the rows of its lower
+// (forward) or upper (backward) entries.  Rows run in level order, each waiting on a
+// per-level completion count (bounded waits; see k_sp_sweep).  A device flag ends the
+// remaining kernels of a batch once PCG has converged.
 #include "sparse.cuh"
 #include "values.cuh"
 
@@ -23,7 +22,6 @@ struct SpState {
     double rho, hn, gstart, rec;
     int32_t iters, done, status, napply;   // napply: preconditioner applications so far
     unsigned err, pad, r0, r1;
-    unsigned ticket[64];                   // one row counter per sweep of an application
 };
 
 struct SpArgs {
@@ -43,6 +41,7 @@ struct SpArgs {
     const int64_t* mptr;
     const int32_t* mcol;
     const void* mval;         // double or float (op dtype)
+    const int64_t* mdiag;     // position of the diagonal in each row
     const double* dinv;
     const int32_t* sched_f;
     const int32_t* sched_b;
@@ -138,7 +137,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_cols(SpArgs a, int use_res, double*
     }
 }
 
-// alpha = rho / p^T w, y += alpha p, g -= alpha w; partial ||g||^2; resets the sweep tickets
+// alpha = rho / p^T w, y += alpha p, g -= alpha w; partial ||g||^2
 __global__ void __launch_bounds__(SP_T) k_sp_update(SpArgs a, int nparts) {
     __shared__ double sh[40];
     if (a.S->done) return;
@@ -179,11 +178,11 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 // warp w takes schedule slots w, w + W, w + 2W, ... (rows sorted by level), so it meets its
 // rows in level order.  A row of level L loads its entries and adds its other-side terms,
 // then waits until every row of level L-1 has finished this sweep: 32 cumulative
-// sub-counters per level (rows add to sub-counter w mod 32, a waiting warp sums all 32 in
-// one load), acquire/release ordering, bounded polls.  Rows of level L depend only on lower
+// sub-counters per level on separate cache lines (rows add to sub-counter w mod 32, a
+// waiting warp sums all 32, one per lane), acquire/release ordering, bounded polls with
+// exponential backoff.  Rows of level L depend only on lower
 // levels, which every warp finishes first, so the wait always ends.
 // `check` (first sweep of an iteration): reduce ||g||^2 first and stop when converged.
-constexpr int SW_SUB = 32;          // sub-counters per level
 constexpr int SW_PF = 16;           // entries per lane held in registers before the wait
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, const double* e_old,
@@ -223,39 +222,35 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
     for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
         const int L = lvl[slot];
-        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1];
-        // entries of the first 32*SW_PF positions, in registers
+        // rows are sorted and hold their diagonal: the dependency side (lower entries forward,
+        // upper backward) and the other side are the two ranges around it
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
+        const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
+        double acc = 0.0;
+        if (other)   // the previous sweep's values: no wait needed
+            for (int64_t e = o0 + lane; e < o1; e += 32) acc = fma((double)mv[e], e_old[a.mcol[e]], acc);
+        // the first 32*SW_PF dependency entries, in registers before the wait
         int32_t kk[SW_PF];
         double mm[SW_PF];
-        double acc = 0.0;
 #pragma unroll
         for (int c = 0; c < SW_PF; ++c) {
-            const int64_t e = e0 + lane + 32 * c;
+            const int64_t e = d0 + lane + 32 * c;
             kk[c] = -1;
             mm[c] = 0.0;
-            if (e < e1) {
-                const int32_t k = a.mcol[e];
-                const double mjk = (double)mv[e];
-                const bool dep = FWD ? (k < j) : (k > j);
-                if (dep) { kk[c] = k; mm[c] = mjk; }
-                else if (other && k != j) acc = fma(mjk, e_old[k], acc);
-            }
-        }
-        for (int64_t e = e0 + lane + 32 * SW_PF; e < e1; e += 32) {   // long rows: rest of the other side
-            const int64_t k = a.mcol[e];
-            if (other && k != j && !(FWD ? (k < j) : (k > j))) acc = fma((double)mv[e], e_old[k], acc);
+            if (e < d1) { kk[c] = a.mcol[e]; mm[c] = (double)mv[e]; }
         }
         if (L > 0) {
             const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
-            const unsigned long long* cnt = done + (int64_t)(L - 1) * SW_SUB;
-            unsigned polls = 0;
+            const unsigned long long* cnt = done + (int64_t)(L - 1) * LVL_WORDS;
+            unsigned polls = 0, ns = 32;
             while (true) {
-                unsigned long long v = ld_acquire_u64(&cnt[lane]);
+                unsigned long long v = ld_acquire_u64(&cnt[lane * LVL_STRIDE]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (v >= target) break;
                 if (++polls > (1u << 22)) { ok = false; break; }
-                if (polls > 8) __nanosleep(32);
+                if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
             }
             // each lane acquired one sub-counter; the warp barrier orders every lane's loads
             // below after all 32 acquires
@@ -264,16 +259,27 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
 #pragma unroll
         for (int c = 0; c < SW_PF; ++c)
             if (kk[c] >= 0) acc = fma(mm[c], e_new[kk[c]], acc);
-        for (int64_t e = e0 + lane + 32 * SW_PF; e < e1; e += 32) {   // long rows: rest of the dependency side
-            const int64_t k = a.mcol[e];
-            if (FWD ? (k < j) : (k > j)) acc = fma((double)mv[e], e_new[k], acc);
+        // long rows: the rest of the dependency side, indices of 8 chunks first, then gathers
+        for (int64_t base = d0 + 32 * SW_PF; base < d1; base += 32 * 8) {
+            int32_t k2[8];
+            double m2[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t e = base + lane + 32 * u;
+                k2[u] = -1;
+                m2[u] = 0.0;
+                if (e < d1) { k2[u] = a.mcol[e]; m2[u] = (double)mv[e]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k2[u] >= 0) acc = fma(m2[u], e_new[k2[u]], acc);
         }
         acc = warp_sum(acc);
         if (lane == 0) {
             const double dj = a.dinv[j];
             const double v = identity ? e_old[j] - acc * dj : (r[j] - acc) * dj;
             e_new[j] = v;
-            red_release_add_u64(&done[(int64_t)L * SW_SUB + (gw & (SW_SUB - 1))], 1ull);
+            red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (gw & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
         }
         __syncwarp();
     }
@@ -310,7 +316,6 @@ __global__ void __launch_bounds__(SP_T) k_sp_pnext(SpArgs a, int first, int npar
             a.S->rho = rho_new;
             a.S->pad = 0;
             a.S->napply += 1;
-            for (int t = 0; t < 2 * a.sweeps; ++t) a.S->ticket[t] = 0;
         }
     }
 }
@@ -393,7 +398,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
     size_t o_S = take(sizeof(SpState)), o_vT = take(es * nnz), o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16),
            o_vec = take(8 * (size_t)n * 10), o_q = take(8 * (size_t)m),
-           o_done = take(8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b)), o_part = take(8 * (size_t)(rblk + 2 * nblk)),
+           o_done = take(8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b)), o_part = take(8 * (size_t)(rblk + 2 * nblk)),
            o_n2 = take(64);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
@@ -408,7 +413,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.valsT = base + o_vT;
     a.valsT_res = res64 ? (DT == LSQ_F64 ? a.valsT : (const void*)(base + o_vT64)) : a.valsT;
     a.inv_d = P->inv_d;
-    a.mptr = SH->mptr; a.mcol = SH->mcol;
+    a.mptr = SH->mptr; a.mcol = SH->mcol; a.mdiag = SH->mdiag;
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
     a.sweeps = P->sweeps;
@@ -417,7 +422,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     double* tmpv = vec + 9 * n;
     a.q = (double*)(base + o_q);
     a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
-    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + SW_SUB * SH->nlev_f;
+    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     auto lanes_for = [](double mean) { int L = 1; while (L < 32 && L < mean) L <<= 1; return L; };
     a.lpr = lanes_for((double)nnz / (double)m);
     a.lpc = lanes_for((double)nnz / (double)n);
@@ -481,7 +486,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     LSQ_CUDA(cudaEventRecord(ev0, st));
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(SpState), st));
-        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b), st));
+        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));
         LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)n, st));
         a.b = B ? B + c * ldb : nullptr;
         a.h_in = Hcols ? Hcols + c * ldb : nullptr;
@@ -612,22 +617,22 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
     size_t o_S = take(sizeof(SpState)), o_e = take(16 * (size_t)n),
-           o_f = take(8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b));
+           o_f = take(8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b));
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
     char* base = sc.as<char>();
     SpArgs a{};
     a.n = n;
-    a.mptr = SH->mptr; a.mcol = SH->mcol;
+    a.mptr = SH->mptr; a.mcol = SH->mcol; a.mdiag = SH->mdiag;
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b; a.sweeps = P->sweeps;
     a.e0 = (double*)(base + o_e); a.e1 = a.e0 + n;
     a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
-    a.done_f = (unsigned long long*)(base + o_f); a.done_b = a.done_f + SW_SUB * SH->nlev_f;
+    a.done_f = (unsigned long long*)(base + o_f); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     a.S = (SpState*)(base + o_S);
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(a.S, 0, sizeof(SpState), st));
-        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)SW_SUB * (SH->nlev_f + SH->nlev_b), st));
+        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));
         const double* rc = r + c * n;
         double* out = e + c * n;
         const double* eold = nullptr;

@@ -25,12 +25,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 
 namespace lsq {
 
 constexpr int BK_T = 256;
 constexpr int BK_MAX = 32;
-constexpr int BK_SUB = 32;     // completion sub-counters per level
 constexpr int BK_PF = 8;       // dependency entries per lane loaded before a level wait
 
 struct BkState {
@@ -60,6 +61,7 @@ struct BkArgs {
     const int64_t* mptr;
     const int32_t* mcol;
     const void* mval;
+    const int64_t* mdiag;
     const double* dinv;
     const int32_t* sched_f;
     const int32_t* sched_b;
@@ -125,7 +127,9 @@ __device__ __forceinline__ void bk_total(const double* part, int nparts, int K, 
 }
 
 // q_i = A_i x, b_i, or b_i - A_i x (mode 0/1/2) for every column; the last block leaves the
-// column sums of ||q||^2 in S->pw
+// column sums of ||q||^2 in S->pw.  A lane group takes 4 consecutive rows and walks their
+// entries flat, 4 at a time, so that several gathers are in flight; each row still sums its
+// entries in order.
 template <int DT>
 __global__ void __launch_bounds__(BK_T) k_bk_rows(BkArgs a, int mode, int use_res, const double* x) {
     __shared__ double sh[BK_T];
@@ -135,17 +139,53 @@ __global__ void __launch_bounds__(BK_T) k_bk_rows(BkArgs a, int mode, int use_re
     const bool col_ok = c < a.K;
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
     const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
+    const int K = a.K;
     double qq = 0.0;
     if (col_ok)
-        for (int64_t i = grp; i < a.m; i += ngrp) {
-            double dot = 0.0;
-            if (mode != 1)
-                for (int64_t e = a.row_ptr[i]; e < a.row_ptr[i + 1]; ++e)
-                    dot = fma(Val<DT>::load(vals, e), x[(int64_t)a.col_idx[e] * a.K + c], dot);
-            const double bi = mode == 0 ? 0.0 : a.b[i * a.K + c];
-            const double qv = mode == 0 ? dot : (mode == 1 ? bi : bi - dot);
-            a.q[i * a.K + c] = qv;
-            qq = fma(qv, qv, qq);
+        for (int64_t i0 = grp * 4; i0 < a.m; i0 += ngrp * 4) {
+            const int nr = (int)min((int64_t)4, a.m - i0);
+            int64_t rp[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r) rp[r] = a.row_ptr[min(i0 + r, a.m)];
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+            if (mode != 1) {
+                const int64_t eend = rp[nr];
+                for (int64_t e = rp[0]; e < eend; e += 4) {
+                    int32_t col[4];
+                    double v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        col[u] = 0;
+                        v[u] = 0.0;
+                        if (e + u < eend) { col[u] = a.col_idx[e + u]; v[u] = Val<DT>::load(vals, e + u); }
+                    }
+                    double xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xv[u] = (e + u < eend) ? x[(int64_t)col[u] * K + c] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t ee = e + u;
+                        if (ee < eend) {
+                            const int r = (ee >= rp[1]) + (ee >= rp[2]) + (ee >= rp[3]);
+                            if (r == 0) d0 = fma(v[u], xv[u], d0);
+                            else if (r == 1) d1 = fma(v[u], xv[u], d1);
+                            else if (r == 2) d2 = fma(v[u], xv[u], d2);
+                            else d3 = fma(v[u], xv[u], d3);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r < nr) {
+                    const int64_t i = i0 + r;
+                    const double dot = r == 0 ? d0 : (r == 1 ? d1 : (r == 2 ? d2 : d3));
+                    const double bi = mode == 0 ? 0.0 : a.b[i * K + c];
+                    const double qv = mode == 0 ? dot : (mode == 1 ? bi : bi - dot);
+                    a.q[i * K + c] = qv;
+                    qq = fma(qv, qv, qq);
+                }
+            }
         }
     bk_block_partials(qq, a.K, a.GK, a.part + (int64_t)blockIdx.x * a.K, sh);
     if (!bk_last_block(&a.S->arrive[0])) return;
@@ -153,7 +193,8 @@ __global__ void __launch_bounds__(BK_T) k_bk_rows(BkArgs a, int mode, int use_re
     if ((int)threadIdx.x < a.K) a.S->pw[threadIdx.x] = sh[threadIdx.x];
 }
 
-// out_j = (1/d_j) A^T_j q for every column (the transposed pattern; no atomics)
+// out_j = (1/d_j) A^T_j q for every column (the transposed pattern; no atomics); entries are
+// loaded 4 at a time before their gathers
 template <int DT>
 __global__ void __launch_bounds__(BK_T) k_bk_cols(BkArgs a, int use_res, double* out) {
     if (a.S->done) return;
@@ -161,12 +202,28 @@ __global__ void __launch_bounds__(BK_T) k_bk_cols(BkArgs a, int use_res, double*
     const int c = threadIdx.x & (a.GK - 1);
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
     const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
-    if (c >= a.K) return;
+    const int K = a.K;
+    if (c >= K) return;
     for (int64_t j = grp; j < a.n; j += ngrp) {
         double t = 0.0;
-        for (int64_t e = a.atptr[j]; e < a.atptr[j + 1]; ++e)
-            t = fma(Val<DT>::load(vals, e), a.q[(int64_t)a.atrow[e] * a.K + c], t);
-        out[j * a.K + c] = t * a.inv_d[j];
+        const int64_t eend = a.atptr[j + 1];
+        for (int64_t e = a.atptr[j]; e < eend; e += 4) {
+            int32_t row[4];
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                row[u] = 0;
+                v[u] = 0.0;
+                if (e + u < eend) { row[u] = a.atrow[e + u]; v[u] = Val<DT>::load(vals, e + u); }
+            }
+            double qv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) qv[u] = (e + u < eend) ? a.q[(int64_t)row[u] * K + c] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u < eend) t = fma(v[u], qv[u], t);
+        }
+        out[j * K + c] = t * a.inv_d[j];
     }
 }
 
@@ -225,11 +282,35 @@ __global__ void __launch_bounds__(BK_T) k_bk_update(BkArgs a) {
     if (threadIdx.x == 0 && !s_any) a.S->done = 1;
 }
 
+// Wait until every row of level L-1 has finished the current sweep: the 32 completion
+// sub-counters of that level (separate cache lines), one per lane, summed by the warp
+// (acquire loads, bounded polls with exponential backoff).
+__device__ __forceinline__ bool bk_level_wait(const unsigned long long* done, int L, unsigned long long epoch,
+                                              const int64_t* lsz, int lane) {
+    if (L == 0) return true;
+    const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
+    const unsigned long long* cntp = done + (int64_t)(L - 1) * LVL_WORDS;
+    unsigned polls = 0, ns = 32;
+    bool ok = true;
+    while (true) {
+        unsigned long long v = bk_ld_acquire_u64(&cntp[lane * LVL_STRIDE]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (v >= target) break;
+        if (++polls > (1u << 22)) { ok = false; break; }
+        if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+    }
+    __syncwarp();
+    return ok;
+}
+
 // One Gauss-Seidel sweep of Alg. 3 for all K columns, level-ordered without grid barriers
-// (cooperative launch; warp w takes schedule slots w, w + W, ...; a row of level L waits on
-// the 32 completion sub-counters of level L-1, bounded polls).  A warp takes a row; the
-// row's entries are loaded 32 at a time and broadcast by shuffles; lane c accumulates
-// column c.  `identity`: the backward sweep right after one forward sweep from zero.
+// (cooperative launch; warp w takes schedule slots w, w + W, ... in level order; a row of
+// level L waits for level L-1).  Rows are sorted and hold their diagonal, so the dependency
+// side (lower entries forward, upper backward) and the other side are the two ranges around
+// it.  This form is for short rows: a warp takes a row, its entries are loaded 32 at a time
+// and broadcast by shuffles, and lane c accumulates column c.  `identity`: the backward sweep
+// right after one forward sweep from zero (e_new = e_old - upper terms / M_jj).
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, const double* e_old,
                                                    double* e_new, int identity, int sweep_idx) {
@@ -251,19 +332,21 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
     for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
         const int L = lvl[slot];
-        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1];
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
+        const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
         double acc = 0.0;
         if (other) {   // previous sweep's values on the other side: no wait needed
-            for (int64_t base = e0; base < e1; base += 32) {
+            for (int64_t base = o0; base < o1; base += 32) {
                 const int64_t e = base + lane;
-                int32_t kk = -1;
+                int32_t kk = 0;
                 double mm = 0.0;
-                if (e < e1) { kk = a.mcol[e]; mm = (double)mv[e]; }
-                const int cnt = (int)min((int64_t)32, e1 - base);
+                if (e < o1) { kk = a.mcol[e]; mm = (double)mv[e]; }
+                const int cnt = (int)min((int64_t)32, o1 - base);
                 for (int t = 0; t < cnt; ++t) {
                     const int32_t k = __shfl_sync(0xffffffffu, kk, t);
                     const double mk = __shfl_sync(0xffffffffu, mm, t);
-                    if ((FWD ? (k > j) : (k < j)) && col_ok) acc = fma(mk, e_old[(int64_t)k * K + lane], acc);
+                    if (col_ok) acc = fma(mk, e_old[(int64_t)k * K + lane], acc);
                 }
             }
         }
@@ -271,47 +354,34 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
         double pm[BK_PF];
 #pragma unroll
         for (int c = 0; c < BK_PF; ++c) {
-            const int64_t e = e0 + lane + 32 * c;
-            pk[c] = -1;
+            const int64_t e = d0 + lane + 32 * c;
+            pk[c] = 0;
             pm[c] = 0.0;
-            if (e < e1) { pk[c] = a.mcol[e]; pm[c] = (double)mv[e]; }
+            if (e < d1) { pk[c] = a.mcol[e]; pm[c] = (double)mv[e]; }
         }
-        if (L > 0) {
-            const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
-            const unsigned long long* cntp = done + (int64_t)(L - 1) * BK_SUB;
-            unsigned polls = 0;
-            while (true) {
-                unsigned long long v = bk_ld_acquire_u64(&cntp[lane]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (v >= target) break;
-                if (++polls > (1u << 22)) { ok = false; break; }
-                if (polls > 8) __nanosleep(32);
-            }
-            __syncwarp();
-        }
+        ok = bk_level_wait(done, L, epoch, lsz, lane) && ok;
 #pragma unroll
         for (int c = 0; c < BK_PF; ++c) {
-            const int64_t cbase = e0 + 32 * c;
-            if (cbase < e1) {
-                const int cnt = (int)min((int64_t)32, e1 - cbase);
+            const int64_t cbase = d0 + 32 * c;
+            if (cbase < d1) {
+                const int cnt = (int)min((int64_t)32, d1 - cbase);
                 for (int t = 0; t < cnt; ++t) {
                     const int32_t k = __shfl_sync(0xffffffffu, pk[c], t);
                     const double mk = __shfl_sync(0xffffffffu, pm[c], t);
-                    if ((FWD ? (k < j) : (k > j)) && col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
+                    if (col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
                 }
             }
         }
-        for (int64_t base = e0 + 32 * BK_PF; base < e1; base += 32) {   // long rows
+        for (int64_t base = d0 + 32 * BK_PF; base < d1; base += 32) {   // long rows
             const int64_t e = base + lane;
-            int32_t kk = -1;
+            int32_t kk = 0;
             double mm = 0.0;
-            if (e < e1) { kk = a.mcol[e]; mm = (double)mv[e]; }
-            const int cnt = (int)min((int64_t)32, e1 - base);
+            if (e < d1) { kk = a.mcol[e]; mm = (double)mv[e]; }
+            const int cnt = (int)min((int64_t)32, d1 - base);
             for (int t = 0; t < cnt; ++t) {
                 const int32_t k = __shfl_sync(0xffffffffu, kk, t);
                 const double mk = __shfl_sync(0xffffffffu, mm, t);
-                if ((FWD ? (k < j) : (k > j)) && col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
+                if (col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
             }
         }
         if (col_ok) {
@@ -320,7 +390,110 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
             e_new[at] = identity ? e_old[at] - acc * dj : (r[at] - acc) * dj;
         }
         __syncwarp();
-        if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * BK_SUB + (gw & (BK_SUB - 1))], 1ull);
+        if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (gw & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
+    }
+    const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
+    if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+}
+
+// acc[0..KT) per lane -> lane l holds the warp total of column l >> (5 - log2 KT)
+// (a butterfly reduce-scatter: each step halves the columns a lane keeps)
+template <int KT>
+__device__ __forceinline__ double bk_reduce_scatter(double (&v)[KT], int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s;
+        const int half = KT >> (s + 1);
+        if (half >= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const double send = upper ? v[i] : v[i + half];
+                const double keep = upper ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+    return v[0];
+}
+
+// The same sweep for long rows: lanes take the row's entries (lane l: entries l, l + 32, ...)
+// and keep KT column accumulators each; one reduce-scatter per row combines them.  The
+// dependency side's first 32*BK_PFE entries are loaded before the level wait.
+constexpr int BK_PFE = 16;
+template <typename MT, bool FWD, int KT>
+__global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r, const double* e_old,
+                                                      double* e_new, int identity, int sweep_idx) {
+    if (a.S->done) return;
+    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
+    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
+    unsigned long long* done = FWD ? a.done_f : a.done_b;
+    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
+    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
+    const int32_t* sched = FWD ? a.sched_f : a.sched_b;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const int lane = threadIdx.x & 31;
+    const int K = a.K;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool other = !identity && e_old != nullptr;
+    constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
+    const int my_col = lane >> SH;
+    const bool writer = (lane & ((1 << SH) - 1)) == 0 && my_col < K;
+    bool ok = true;
+    for (int64_t slot = gw; slot < a.n; slot += W) {
+        const int64_t j = sched[slot];
+        const int L = lvl[slot];
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
+        const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
+        double acc[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) acc[c] = 0.0;
+        if (other)
+            for (int64_t e = o0 + lane; e < o1; e += 32) {
+                const int64_t k = a.mcol[e];
+                const double mk = (double)mv[e];
+#pragma unroll
+                for (int c = 0; c < KT; ++c)
+                    if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
+            }
+        int32_t pk[BK_PFE];
+        double pm[BK_PFE];
+#pragma unroll
+        for (int u = 0; u < BK_PFE; ++u) {
+            const int64_t e = d0 + lane + 32 * u;
+            pk[u] = -1;
+            pm[u] = 0.0;
+            if (e < d1) { pk[u] = a.mcol[e]; pm[u] = (double)mv[e]; }
+        }
+        ok = bk_level_wait(done, L, epoch, lsz, lane) && ok;
+#pragma unroll
+        for (int u = 0; u < BK_PFE; ++u) {
+            if (pk[u] >= 0) {
+                const double* row = e_new + (int64_t)pk[u] * K;
+#pragma unroll
+                for (int c = 0; c < KT; ++c)
+                    if (c < K) acc[c] = fma(pm[u], row[c], acc[c]);
+            }
+        }
+        for (int64_t e = d0 + lane + 32 * BK_PFE; e < d1; e += 32) {   // very long rows
+            const double* row = e_new + (int64_t)a.mcol[e] * K;
+            const double mk = (double)mv[e];
+#pragma unroll
+            for (int c = 0; c < KT; ++c)
+                if (c < K) acc[c] = fma(mk, row[c], acc[c]);
+        }
+        const double tot = bk_reduce_scatter<KT>(acc, lane);
+        if (writer) {
+            const double dj = a.dinv[j];
+            const int64_t at = j * K + my_col;
+            e_new[at] = identity ? e_old[at] - tot * dj : (r[at] - tot) * dj;
+        }
+        __syncwarp();
+        if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (gw & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
     }
     const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
     if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
@@ -429,24 +602,43 @@ static unsigned bk_grid(int64_t work, int64_t cap) {
 }
 
 // Cooperative launch: every warp of the sweep must be resident for the level waits to end.
-template <typename MT, bool FWD>
-static lsq_status bk_launch_sweep(const BkArgs& a, const double* r, const double* eold, double* enew,
-                                  int identity, int idx, cudaStream_t st) {
-    static int grid = 0;
-    auto kern = k_bk_sweep<MT, FWD>;
-    if (grid == 0) {
-        int dev = 0, sms = 0, per = 0;
-        LSQ_CUDA(cudaGetDevice(&dev));
-        LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BK_T, 0));
-        if (per < 1) { set_error("block sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
-        grid = sms * per;
+// The grid (SMs x resident blocks) is computed once per kernel.
+static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const double* r, const double* eold,
+                                  double* enew, int identity, int idx, cudaStream_t st) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> grids;
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = grids.find(kern);
+        if (it != grids.end()) {
+            grid = it->second;
+        } else {
+            int dev = 0, sms = 0, per = 0;
+            LSQ_CUDA(cudaGetDevice(&dev));
+            LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BK_T, 0));
+            if (per < 1) { set_error("block sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
+            grid = sms * per;
+            grids[kern] = grid;
+        }
     }
     BkArgs av = a;
     void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &idx};
-    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(BK_T), params, 0, st));
+    LSQ_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BK_T), params, 0, st));
     count_launch();
     return LSQ_OK;
+}
+
+// lane-per-column sweep for short rows, entry-parallel sweep (KT >= K accumulators) for long
+template <typename MT, bool FWD>
+static const void* bk_sweep_kernel(bool ep, int K) {
+    if (!ep) return (const void*)k_bk_sweep<MT, FWD>;
+    if (K <= 2) return (const void*)k_bk_sweep_ep<MT, FWD, 2>;
+    if (K <= 4) return (const void*)k_bk_sweep_ep<MT, FWD, 4>;
+    if (K <= 8) return (const void*)k_bk_sweep_ep<MT, FWD, 8>;
+    if (K <= 16) return (const void*)k_bk_sweep_ep<MT, FWD, 16>;
+    return (const void*)k_bk_sweep_ep<MT, FWD, 32>;
 }
 
 struct BkOut {
@@ -475,7 +667,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     const size_t o_S = take(sizeof(BkState)), o_vT = take(es * nnz),
                  o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16), o_vec = take(8 * (size_t)nK * 10),
                  o_q = take(8 * (size_t)m * K), o_b = take(B ? 8 * (size_t)m * K : 16),
-                 o_done = take(8 * (size_t)BK_SUB * (SH->nlev_f + SH->nlev_b)),
+                 o_done = take(8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b)),
                  o_part = take(8 * (size_t)2 * grid_cap * K), o_n2 = take(8 * 2 * BK_MAX);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
@@ -491,11 +683,11 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.valsT_res = res64 ? (DT == LSQ_F64 ? a.valsT : (const void*)(base + o_vT64)) : a.valsT;
     a.inv_d = P->inv_d;
     a.b = B ? (const double*)(base + o_b) : nullptr;
-    a.mptr = SH->mptr; a.mcol = SH->mcol;
+    a.mptr = SH->mptr; a.mcol = SH->mcol; a.mdiag = SH->mdiag;
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
     a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
-    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + BK_SUB * SH->nlev_f;
+    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     a.sweeps = P->sweeps;
     a.y = vec; a.g = vec + nK; a.z = vec + 2 * nK; a.p = vec + 3 * nK; a.pt = vec + 4 * nK;
     a.w = vec + 5 * nK; a.e0 = vec + 6 * nK; a.e1 = vec + 7 * nK; a.h = vec + 8 * nK;
@@ -530,15 +722,14 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         else k_bk_cols<DT><<<gcols, BK_T, 0, st>>>(a, 0, dst);
         count_launch();
     };
+    // rows whose dependency side averages more than 24 entries take the entry-parallel sweep
+    const bool ep = (double)(SH->nnz_M - n) / (2.0 * (double)n) > 24.0;
+    const bool m32 = P->op_dtype == LSQ_F32;
+    const void* kf = m32 ? bk_sweep_kernel<float, true>(ep, K) : bk_sweep_kernel<double, true>(ep, K);
+    const void* kb = m32 ? bk_sweep_kernel<float, false>(ep, K) : bk_sweep_kernel<double, false>(ep, K);
     lsq_status sweep_status = LSQ_OK;
     auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int idx) {
-        lsq_status q;
-        if (P->op_dtype == LSQ_F32)
-            q = fwd ? bk_launch_sweep<float, true>(a, r, eold, enew, identity, idx, st)
-                    : bk_launch_sweep<float, false>(a, r, eold, enew, identity, idx, st);
-        else
-            q = fwd ? bk_launch_sweep<double, true>(a, r, eold, enew, identity, idx, st)
-                    : bk_launch_sweep<double, false>(a, r, eold, enew, identity, idx, st);
+        lsq_status q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, st);
         if (q != LSQ_OK) sweep_status = q;
     };
     // z = P g: t forward then t backward sweeps
@@ -569,7 +760,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         return LSQ_OK;
     };
     LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(BkState), st));
-    LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)BK_SUB * (SH->nlev_f + SH->nlev_b), st));
+    LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));
     LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)nK, st));
     if (Hcols) {
         k_bk_to_rows<<<bk_grid(nK, 4096), BK_T, 0, st>>>(Hcols, ldb, n, K, a.h);

@@ -12,6 +12,7 @@ struct SparseHandle {
     double* mval = nullptr;
     float* mval32 = nullptr;    // FP32 copy when the operator dtype is F32
     double* dinv = nullptr;     // 1 / M_jj
+    int64_t* mdiag = nullptr;   // position of M_jj in row j (rows are sorted, the diagonal is stored)
     // rows listed by forward / backward level (Gauss-Seidel dependency order)
     int32_t* sched_f = nullptr;
     int32_t* sched_b = nullptr;
@@ -25,6 +26,13 @@ struct SparseHandle {
     int32_t* atrow = nullptr;
     int64_t* atperm = nullptr;
 };
+
+// Level completion counters of the sparse sweeps: LVL_SUB cumulative sub-counters per level,
+// each on its own 128-byte line (LVL_STRIDE 8-byte words apart) so that polls and updates
+// spread over L2 slices.
+constexpr int LVL_SUB = 32;
+constexpr int LVL_STRIDE = 16;
+constexpr int64_t LVL_WORDS = (int64_t)LVL_SUB * LVL_STRIDE;
 
 lsq_status scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* scratch, cudaStream_t st);
 lsq_status transpose_pattern(const int64_t* rptr, const int32_t* col, int64_t nr, int64_t nc, int64_t nnz,

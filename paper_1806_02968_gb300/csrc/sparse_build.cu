@@ -377,12 +377,15 @@ __global__ void __launch_bounds__(SPG_T) k_spgemm_row(
 }
 
 // diagonal inverse of M (the diagonal is always stored)
-__global__ void k_diag_inv(const int64_t* mptr, const int32_t* mcol, const double* mval, int64_t n, double* dinv) {
+__global__ void k_diag_inv(const int64_t* mptr, const int32_t* mcol, const double* mval, int64_t n, double* dinv,
+                           int64_t* mdiag) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         double v = 1.0;
+        int64_t at = mptr[j];
         for (int64_t e = mptr[j]; e < mptr[j + 1]; ++e)
-            if (mcol[e] == j) { v = mval[e]; break; }
+            if (mcol[e] == j) { v = mval[e]; at = e; break; }
         dinv[j] = 1.0 / v;
+        mdiag[j] = at;
     }
 }
 __global__ void k_to_f32(const double* src, float* dst, int64_t count) {
@@ -531,7 +534,8 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
                                        S->mcol, S->mval, nfix, err);
     count_launch();
     LSQ_CUDA(cudaMalloc(&S->dinv, 8 * (size_t)n));
-    k_diag_inv<<<grid1(n), 256, 0, st>>>(S->mptr, S->mcol, S->mval, n, S->dinv);
+    LSQ_CUDA(cudaMalloc(&S->mdiag, 8 * (size_t)n));
+    k_diag_inv<<<grid1(n), 256, 0, st>>>(S->mptr, S->mcol, S->mval, n, S->dinv, S->mdiag);
     count_launch();
     if (H->op_dtype == LSQ_F32) {
         LSQ_CUDA(cudaMalloc(&S->mval32, 4 * (size_t)mnnz));
@@ -582,7 +586,7 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
 
 void free_sparse(SparseHandle* S) {
     if (!S) return;
-    cudaFree(S->mptr); cudaFree(S->mcol); cudaFree(S->mval); cudaFree(S->mval32); cudaFree(S->dinv);
+    cudaFree(S->mptr); cudaFree(S->mcol); cudaFree(S->mval); cudaFree(S->mval32); cudaFree(S->dinv); cudaFree(S->mdiag);
     cudaFree(S->sched_f); cudaFree(S->sched_b); cudaFree(S->lvl_f); cudaFree(S->lvl_b);
     cudaFree(S->lsize_f); cudaFree(S->lsize_b); cudaFree(S->atptr); cudaFree(S->atrow);
     cudaFree(S->atperm);

@@ -37,7 +37,7 @@ def test_sparse_normal_matrix_pattern_and_values(lsq, orc, case):
 
 
 @pytest.mark.parametrize("sweeps", [1, 2])
-@pytest.mark.parametrize("case", ["sprand", "graph"])
+@pytest.mark.parametrize("case", ["sprand", "graph", "wide"])
 def test_sparse_sweeps_match_alg3(lsq, orc, case, sweeps):
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003, sweeps=sweeps)
     rng = np.random.default_rng(sweeps)
@@ -167,3 +167,20 @@ def test_sparse_block_f32_refinement(lsq, orc):
     X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
     for c in range(4):
         assert info.converged[c] == 1 and info.relres_true[c] <= o.tol
+
+
+@pytest.mark.parametrize("case,k", [("sprand", 3), ("wide", 2)])
+def test_sparse_block_long_rows_two_sweeps(lsq, orc, case, k):
+    """M rows of hundreds of entries take the entry-parallel block sweep; t = 2 also
+    exercises its other-side terms (the previous sweep's values)."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 313, sweeps=2)
+    xs, b = W.rhs_for(seen, k, 1e-3, 31)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    A = W.dense_from_csr(seen)
+    kappa = np.linalg.cond(A / smp.d)
+    for c in range(k):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=2)
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])

@@ -250,3 +250,41 @@ def solve(A: Matrix, b, o=None, stream=None):
     P = lsq_build_precond(A, idx, p, d, o, stream=stream)
     x, info = lsq_pcg_solve(A, P, b, o, stream=stream)
     return x, info, dict(idx=idx, p=p, colscale=d, P=P)
+
+
+class LsqSolveFunction(torch.autograd.Function):
+    """X = argmin_X ||A X - B|| (Alg. 2 step 4) as an autograd node.
+
+    Backward reuses the sampled SGS preconditioner for the adjoint system A^T A lambda = dL/dX
+    (lsq_pcg_adjoint), giving dL/dB = A lambda and dL/dA = r lambda^T - (A lambda) x^T (summed
+    over the right-hand sides), restricted to A's pattern for a CSR matrix.  Inputs: A's value
+    tensor (the one `A` was built from), B ((m,) or (k, m) float64), then the Matrix, the
+    Precond and the options, which take no gradient."""
+
+    @staticmethod
+    def forward(ctx, vals, B, A, P, o):
+        if A.dtype == L.LSQ_F32X2:
+            raise ValueError("differentiation needs plain FP64/FP32/BF16 values")
+        if vals.data_ptr() != A.vals.data_ptr():
+            raise ValueError("vals must be the tensor the Matrix was built from")
+        X, info = lsq_pcg_solve(A, P, B, o)
+        ctx.A, ctx.P, ctx.o = A, P, o
+        ctx.vals_shape, ctx.vals_dtype = vals.shape, vals.dtype
+        ctx.info = info
+        ctx.save_for_backward(X, B)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        X, B = ctx.saved_tensors
+        need_v, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        G = gX.to(torch.float64).contiguous()
+        gb, gv, lam, info = lsq_pcg_adjoint(ctx.A, ctx.P, X, B, G, ctx.o, want_grad_vals=need_v)
+        grad_vals = gv.reshape(ctx.vals_shape).to(ctx.vals_dtype) if need_v else None
+        grad_b = gb.reshape(B.shape) if need_b else None
+        return grad_vals, grad_b, None, None, None
+
+
+def lsq_solve(A: Matrix, B, P: Precond, o=None):
+    """Differentiable solve: gradients flow to A.vals and B (see LsqSolveFunction)."""
+    return LsqSolveFunction.apply(A.vals, B, A, P, o or opts())

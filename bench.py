@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
-    ap.add_argument("--workload", choices=["udv", "sparse", "graph", "adjoint"], default="udv",
+    ap.add_argument("--workload", choices=["udv", "sparse", "graph", "adjoint", "batch"], default="udv",
                     help="udv: the timed benchmark; the others measure the CSR configurations")
     return ap.parse_args()
 
@@ -401,10 +401,129 @@ def run_sparse_workload(args):
     print(json.dumps(line), flush=True)
 
 
+# FP32 FMA peak of the batch kernel's arithmetic: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_batch_workload(args):
+    """64 uneven dense Gaussian problems (m log-uniform in [1024, 16384], n in [32, 256]),
+    16 right-hand sides each, FP32 values: all PCG solves in one launch (lsq_batch_solve,
+    replayed from a captured CUDA graph), against the same problems solved one at a time
+    with FP64 values (lsq_pcg_solve)."""
+    import torch
+    import workloads as W
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    from paper_1806_02968_gb300 import api
+    torch.cuda.set_device(0)
+    count, k = 64, 16
+    mats = W.uneven_dense_batch(count, (1024, 16384), (32, 256), 5)
+    o = api.opts(tol=args.tol, maxit=min(args.maxit, 100000), max_outer=30, inner_tol=1e-4)
+    probs, keep = [], []
+    t0 = time.perf_counter()
+    for i, mt in enumerate(mats):
+        A64 = np.asarray(mt["A"])
+        m, n = A64.shape
+        ld = (n + 3) // 4 * 4
+        T = torch.zeros(m, ld, dtype=torch.float32, device="cuda")
+        T[:, :n] = torch.from_numpy(A64).float().cuda()
+        seen = {"kind": "dense", "A": T[:, :n].double().cpu().numpy()}
+        xs, b = W.rhs_for(seen, k, 1e-3, 100 + i)
+        keep.append((T, seen, torch.from_numpy(b).cuda()))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for i, (T, seen, B) in enumerate(keep):
+        n = seen["A"].shape[1]
+        Mx = api.Matrix(T[:, :n])
+        po = api.opts(seed=200 + i, precond_dtype=1)
+        idx, p, d = api.lsq_sample_rows(Mx, po)
+        P = api.lsq_build_precond(Mx, idx, p, d, po)
+        probs.append((T, n, P, B))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    bt = api.Batch(probs, o)
+    cluster = bt.autotune()
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            bt.solve(stream=stream)
+    torch.cuda.synchronize()
+    L0 = api.launches()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1) / args.steps
+    infos = bt.info()
+    iters = np.array([inf.iters for inf in infos])
+    outers = np.array([inf.outer for inf in infos])
+    conv = np.array([inf.converged for inf in infos])
+    tru = np.array([inf.relres_true for inf in infos])
+    # algorithmic work of one launch: per problem, one pass over A (FP32) per inner iteration
+    # of its slowest column and one FP64 residual pass per (re)start plus the final check
+    byts, flops = 0.0, 0.0
+    for (T, n, P, B), it, ou in zip(probs, iters, outers):
+        m = T.shape[0]
+        passes = int(it.max()) + int(ou.max()) + 1
+        byts += passes * m * T.shape[1] * 4.0
+        flops += int(it.max()) * 4.0 * m * n * k
+    # the same problems, one at a time, FP64 values (the plain GPU solve), solves only
+    singles = []
+    for i, (T, seen, B) in enumerate(keep):
+        A64 = torch.from_numpy(seen["A"]).cuda()
+        M64 = api.Matrix(A64)
+        po = api.opts(seed=200 + i)
+        idx, p, d = api.lsq_sample_rows(M64, po)
+        singles.append((A64, M64, api.lsq_build_precond(M64, idx, p, d, po), B))
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f64_iters = []
+    f0.record()
+    for A64, M64, P64, B in singles:
+        X64, inf64 = api.lsq_pcg_solve(M64, P64, B, api.opts(tol=args.tol))
+        f64_iters.append(int(inf64.iters.max()))
+    f1.record()
+    torch.cuda.synchronize()
+    f64_ms = f0.elapsed_time(f1)
+    line = {"metric": METRIC, "value": count * k / (solve_ms / 1e3), "unit": "solves/s (right-hand sides)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_ms,
+            "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "uneven_dense_batch_64x16rhs", "count": count, "k": k,
+                       "m_range": [1024, 16384], "n_range": [32, 256], "tol": args.tol,
+                       "A_bytes": int(sum(T.numel() * 4 for T, _, _, _ in probs)), "cluster": cluster,
+                       "l2": "A (about the L2 size) stays resident across replays"},
+            "gpu_launches": (api.launches() - L0) // max(1, args.warmup + args.steps),
+            "roofline": {"bound": "alu", "achieved": flops / (solve_ms / 1e3) / 1e12,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / (solve_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_pcg_batch", "hbm_gbs": byts / (solve_ms / 1e3) / 1e9,
+                         "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"},
+            "phases": {"gen_s": t1 - t0, "setup_s": t2 - t1, "plan_autotune_s": t3 - t2,
+                       "solve_ms": solve_ms, "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
+                       "outer_max": int(outers.max()), "converged": int(conv.sum()),
+                       "relres_true_max": float(tru.max()),
+                       "f64_one_at_a_time_ms": f64_ms, "f64_iters_mean": float(np.mean(f64_iters)),
+                       "speedup_vs_f64_single": f64_ms / solve_ms}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_workload(args)
     elif args.workload != "udv":
         run_sparse_workload(args)
     else:

@@ -253,6 +253,60 @@ LSQ_API lsq_status lsq_pcg_adjoint(const lsq_matrix* A, const lsq_precond* P, co
                            int64_t ldx, double* grad_b, double* grad_vals, double* Lambda,
                            const lsq_opts* o, lsq_info* info, void* stream);
 
+/*
+ * Batches of small dense problems (the batching extension; not in the paper, which solves
+ * one problem at a time).  Every problem is an independent instance of Alg. 2 step 4 with
+ * its own preconditioner; lsq_batch_solve runs the PCG of all of them in ONE kernel launch.
+ *
+ * lsq_batch_problem: one problem.
+ *   m, n, ld   A is m x n, row-major with leading dimension ld; 1 <= n <= 256, n <= ld,
+ *              ld a multiple of 4, m >= 1
+ *   A          device float, 16-byte aligned.  Entries A[i*ld + j] with n <= j < ld are
+ *              never used.  FP32 is the storage and the arithmetic of the inner iteration;
+ *              restarts use the FP64 residual of the same values.
+ *   P          dense handle from lsq_build_precond for this A (any precond_dtype, sweeps)
+ *   B, ldb     device double, k right-hand sides, column c at B + c*ldb (ldb >= m)
+ *   X, ldx     device double, k solutions, column c at X + c*ldx (ldx >= n) (output)
+ * Every pointer is borrowed and must stay valid for the life of the plan.
+ *
+ * lsq_batch_create   copies the problem table to the device, assigns problems to thread-block
+ *                    clusters (largest first, each to the least loaded cluster), allocates
+ *                    the workspace.  1 <= k <= 16.  o: tol, maxit, max_outer, inner_tol.
+ *                    Synchronises the stream.  *out is library-owned.
+ * lsq_batch_solve    one launch, stream-ordered, no host synchronisation and no allocation:
+ *                    can be captured in a CUDA graph.  Results go to the plan's device
+ *                    status table.
+ * lsq_batch_autotune times lsq_batch_solve for each cluster size that fits (1, 2, 4, 8 and,
+ *                    where the device allows it, 16 CTAs per problem) and keeps the fastest;
+ *                    *cluster_out (may be NULL) receives it.  The solutions are those of a
+ *                    final run with the chosen size.  Synchronises the stream.
+ * lsq_batch_set_cluster  choose the cluster size by hand (1, 2, 4, 8, 16); LSQ_ERR_UNSUPPORTED
+ *                    if the device cannot run it.
+ * lsq_batch_info     copies the per-problem, per-column results of the last solve into
+ *                    infos[p] (host, count entries; arrays of length >= k) and synchronises;
+ *                    returns LSQ_ERR_NOT_CONVERGED if any column missed the tolerance.
+ * lsq_batch_destroy  frees the plan (NULL is ignored) after synchronising its stream.
+ */
+typedef struct {
+    int64_t m, n, ld;
+    const float* A;
+    const lsq_precond* P;
+    const double* B;
+    int64_t ldb;
+    double* X;
+    int64_t ldx;
+} lsq_batch_problem;
+
+typedef struct lsq_batch lsq_batch;
+
+LSQ_API lsq_status lsq_batch_create(const lsq_batch_problem* probs, int64_t count, int64_t k,
+                                    const lsq_opts* o, lsq_batch** out, void* stream);
+LSQ_API lsq_status lsq_batch_solve(lsq_batch* b, void* stream);
+LSQ_API lsq_status lsq_batch_autotune(lsq_batch* b, int32_t* cluster_out, void* stream);
+LSQ_API lsq_status lsq_batch_set_cluster(lsq_batch* b, int32_t cluster);
+LSQ_API lsq_status lsq_batch_info(const lsq_batch* b, lsq_info* infos, void* stream);
+LSQ_API void lsq_batch_destroy(lsq_batch* b);
+
 /* Convert FP64 values to the LSQ_F32X2 pair format (hi = RN(v), lo = RN(v - hi)),
  * count elements, device to device. */
 LSQ_API lsq_status lsq_split_f64(const double* src, float* dst_pairs, int64_t count, void* stream);

@@ -34,6 +34,12 @@ class LsqInfo(C.Structure):
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
 
 
+class LsqBatchProblem(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ld", C.c_int64), ("A", C.c_void_p),
+                ("P", C.c_void_p), ("B", C.c_void_p), ("ldb", C.c_int64), ("X", C.c_void_p),
+                ("ldx", C.c_int64)]
+
+
 # name -> (restype, argtypes)
 P, I64, D = C.c_void_p, C.c_int64, C.c_double
 PROTOTYPES = {
@@ -50,6 +56,12 @@ PROTOTYPES = {
     "lsq_pcg_solve": (C.c_int, [P, P, P, I64, I64, P, I64, P, P, P]),
     "lsq_pcg_adjoint": (C.c_int, [P, P, P, P, P, I64, I64, I64, P, P, P, P, P, P]),
     "lsq_split_f64": (C.c_int, [P, P, I64, P]),
+    "lsq_batch_create": (C.c_int, [P, I64, I64, P, P, P]),
+    "lsq_batch_solve": (C.c_int, [P, P]),
+    "lsq_batch_autotune": (C.c_int, [P, P, P]),
+    "lsq_batch_set_cluster": (C.c_int, [P, C.c_int32]),
+    "lsq_batch_info": (C.c_int, [P, P, P]),
+    "lsq_batch_destroy": (None, [P]),
     "lsq_status_string": (C.c_char_p, [C.c_int]),
     "lsq_last_error_string": (C.c_char_p, []),
     "lsq_kernel_launch_count": (I64, []),

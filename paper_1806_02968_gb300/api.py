@@ -252,6 +252,65 @@ def solve(A: Matrix, b, o=None, stream=None):
     return x, info, dict(idx=idx, p=p, colscale=d, P=P)
 
 
+class Batch:
+    """A plan for many small dense problems solved in one launch (lsq_batch_* calls).
+
+    problems: list of (A float32 (m, ld) row-major with ld % 4 == 0 (the first n columns are
+    the matrix), n, Precond, B float64 (k, m)).  Solutions are written to X[p] (k, n)."""
+
+    def __init__(self, problems, o=None, stream=None):
+        self.o = o or opts()
+        self.keep = []
+        self.k = problems[0][3].shape[0] if problems[0][3].dim() == 2 else 1
+        self.X = []
+        arr = (L.LsqBatchProblem * len(problems))()
+        for i, (A, n, P, B) in enumerate(problems):
+            B2 = B.reshape(1, -1) if B.dim() == 1 else B
+            assert A.dtype == torch.float32 and A.is_cuda and A.stride(1) == 1
+            assert B2.dtype == torch.float64 and B2.stride(1) == 1 and B2.shape[0] == self.k
+            X = torch.zeros(self.k, n, dtype=torch.float64, device=A.device)
+            self.keep += [A, B2, P]
+            self.X.append(X)
+            arr[i] = L.LsqBatchProblem(A.shape[0], n, A.stride(0), A.data_ptr(), P.h, B2.data_ptr(),
+                                       B2.stride(0), X.data_ptr(), X.stride(0))
+        self.count = len(problems)
+        h = C.c_void_p()
+        _check(L.load().lsq_batch_create(arr, self.count, self.k, C.byref(self.o), C.byref(h),
+                                         _stream(stream)), "lsq_batch_create")
+        self.h = h
+
+    def solve(self, stream=None):
+        """One launch; no host synchronisation (may be captured in a CUDA graph)."""
+        _check(L.load().lsq_batch_solve(self.h, _stream(stream)), "lsq_batch_solve")
+
+    def autotune(self, stream=None) -> int:
+        c = C.c_int32()
+        _check(L.load().lsq_batch_autotune(self.h, C.byref(c), _stream(stream)), "lsq_batch_autotune")
+        return c.value
+
+    def set_cluster(self, cluster: int):
+        _check(L.load().lsq_batch_set_cluster(self.h, int(cluster)), "lsq_batch_set_cluster")
+
+    def info(self, stream=None):
+        """Per-problem Info of the last solve."""
+        cis = (L.LsqInfo * self.count)()
+        arrs = []
+        for p in range(self.count):
+            ci, a = _info(self.k)
+            cis[p] = ci
+            arrs.append(a)
+        code = L.load().lsq_batch_info(self.h, cis, _stream(stream))
+        if code not in ACCEPT:
+            raise L.LsqError(code, "lsq_batch_info")
+        return [_finish_info(cis[p], arrs[p], code) for p in range(self.count)]
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            L.load().lsq_batch_destroy(h)
+            self.h = None
+
+
 class LsqSolveFunction(torch.autograd.Function):
     """X = argmin_X ||A X - B|| (Alg. 2 step 4) as an autograd node.
 

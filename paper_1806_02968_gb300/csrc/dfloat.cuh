@@ -42,6 +42,26 @@ __device__ __forceinline__ void df_fma(f2& acc, f2 a, f2 b) {
     acc.lo = e - (hi - s);
     acc.hi = hi;
 }
+// acc += a * b in the cascaded form of Ogita, Rump & Oishi's Dot2 (SIAM J. Sci. Comput.
+// 26(6), 2005): the high word takes the rounded sum, the two-sum and product errors are
+// summed into the low word without renormalising.  acc is then an unevaluated pair whose
+// low word may exceed ulp(hi)/2; df_norm restores the normal form.  The result keeps the
+// accuracy of twice the working precision.
+__device__ __forceinline__ void df_fma_cascade(f2& acc, f2 a, f2 b) {
+    float p, pe;
+    two_prod(a.hi, b.hi, p, pe);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo += e + pe;
+}
+// the normal form of a cascaded pair (|lo| small against |hi|: a fast two-sum suffices)
+__device__ __forceinline__ f2 df_norm(f2 v) {
+    const float hi = v.hi + v.lo;
+    return f2{hi, v.lo - (hi - v.hi)};
+}
 // acc += a * a for a single float a (exact square folded into a double-float sum)
 __device__ __forceinline__ void df_add_sq(f2& acc, float a) {
     float p, pe;

@@ -269,15 +269,17 @@ template <int NMAX> struct RowOps<LSQ_F32X2, NMAX> {
                     const float4 sx = *reinterpret_cast<const float4*>(sv + col);   // two pairs
                     const bool in1 = col + 1 < n;
                     const float4 v = *reinterpret_cast<const float4*>(r0 + 2 * col);  // hi0 lo0 hi1 lo1
-                    df_fma(d0[(2 * c) & 3], f2{v.x, v.y}, f2{sx.x, sx.y});
-                    if (in1) df_fma(d0[(2 * c + 1) & 3], f2{v.z, v.w}, f2{sx.z, sx.w});
+                    df_fma_cascade(d0[(2 * c) & 3], f2{v.x, v.y}, f2{sx.x, sx.y});
+                    if (in1) df_fma_cascade(d0[(2 * c + 1) & 3], f2{v.z, v.w}, f2{sx.z, sx.w});
                     if (TWO) {
                         const float4 w = *reinterpret_cast<const float4*>(r1 + 2 * col);
-                        df_fma(d1[(2 * c) & 3], f2{w.x, w.y}, f2{sx.x, sx.y});
-                        if (in1) df_fma(d1[(2 * c + 1) & 3], f2{w.z, w.w}, f2{sx.z, sx.w});
+                        df_fma_cascade(d1[(2 * c) & 3], f2{w.x, w.y}, f2{sx.x, sx.y});
+                        if (in1) df_fma_cascade(d1[(2 * c + 1) & 3], f2{w.z, w.w}, f2{sx.z, sx.w});
                     }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { d0[k] = df_norm(d0[k]); d1[k] = df_norm(d1[k]); }
             df_add(d0[0], d0[1]); df_add(d0[2], d0[3]); df_add(d0[0], d0[2]);
             df_add(d1[0], d1[1]); df_add(d1[2], d1[3]); df_add(d1[0], d1[2]);
             f2 d0a = d0[0], d1a = d1[0];
@@ -295,12 +297,12 @@ template <int NMAX> struct RowOps<LSQ_F32X2, NMAX> {
             if (col < n) {
                 const bool in1 = col + 1 < n;
                 const float4 v = *reinterpret_cast<const float4*>(r0 + 2 * col);
-                df_fma(A.v[c][0], q0, f2{v.x, v.y});
-                if (in1) df_fma(A.v[c][1], q0, f2{v.z, v.w});
+                df_fma_cascade(A.v[c][0], q0, f2{v.x, v.y});
+                if (in1) df_fma_cascade(A.v[c][1], q0, f2{v.z, v.w});
                 if (TWO) {
                     const float4 w = *reinterpret_cast<const float4*>(r1 + 2 * col);
-                    df_fma(A.v[c][0], q1, f2{w.x, w.y});
-                    if (in1) df_fma(A.v[c][1], q1, f2{w.z, w.w});
+                    df_fma_cascade(A.v[c][0], q1, f2{w.x, w.y});
+                    if (in1) df_fma_cascade(A.v[c][1], q1, f2{w.z, w.w});
                 }
             }
         }
@@ -309,8 +311,8 @@ template <int NMAX> struct RowOps<LSQ_F32X2, NMAX> {
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             const int col = c * 32 * VEC + lane * VEC;
-            *reinterpret_cast<float4*>(dst + col) =
-                make_float4(A.v[c][0].hi, A.v[c][0].lo, A.v[c][1].hi, A.v[c][1].lo);
+            const f2 a0 = df_norm(A.v[c][0]), a1 = df_norm(A.v[c][1]);
+            *reinterpret_cast<float4*>(dst + col) = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
         }
     }
     static __device__ __forceinline__ void red_add(RT& acc, RT v) { df_add(acc, v); }

@@ -499,6 +499,98 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r,
     if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
+// The same sweep for very long rows: a whole CTA takes a row (CTA b: schedule slots b, b + G,
+// ... in level order).  Thread t takes entries t, t + 256, ... of the row and keeps KT column
+// accumulators; warp 0 waits for the previous level and a block barrier releases the others;
+// each warp reduce-scatters its accumulators and the warps' partials are added in warp order.
+constexpr int BK_PFC = 2;
+template <typename MT, bool FWD, int KT>
+__global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r, const double* e_old,
+                                                       double* e_new, int identity, int sweep_idx) {
+    __shared__ double s_part[BK_T / 32][KT];
+    __shared__ int s_bad;
+    if (a.S->done) return;
+    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
+    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
+    unsigned long long* done = FWD ? a.done_f : a.done_b;
+    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
+    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
+    const int32_t* sched = FWD ? a.sched_f : a.sched_b;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int K = a.K;
+    const bool other = !identity && e_old != nullptr;
+    constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int64_t slot = blockIdx.x; slot < a.n; slot += gridDim.x) {
+        const int64_t j = sched[slot];
+        const int L = lvl[slot];
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
+        const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
+        double acc[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) acc[c] = 0.0;
+        if (other)
+            for (int64_t e = o0 + tid; e < o1; e += BK_T) {
+                const int64_t k = a.mcol[e];
+                const double mk = (double)mv[e];
+#pragma unroll
+                for (int c = 0; c < KT; ++c)
+                    if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
+            }
+        int32_t pk[BK_PFC];
+        double pm[BK_PFC];
+#pragma unroll
+        for (int u = 0; u < BK_PFC; ++u) {
+            const int64_t e = d0 + tid + BK_T * u;
+            pk[u] = -1;
+            pm[u] = 0.0;
+            if (e < d1) { pk[u] = a.mcol[e]; pm[u] = (double)mv[e]; }
+        }
+        if (wid == 0) {
+            const bool ok = bk_level_wait(done, L, epoch, lsz, lane);
+            if (!ok && lane == 0) s_bad = 1;
+            __threadfence();
+        }
+        __syncthreads();   // the level's rows are visible to every warp of the CTA
+#pragma unroll
+        for (int u = 0; u < BK_PFC; ++u) {
+            if (pk[u] >= 0) {
+                const double* row = e_new + (int64_t)pk[u] * K;
+#pragma unroll
+                for (int c = 0; c < KT; ++c)
+                    if (c < K) acc[c] = fma(pm[u], row[c], acc[c]);
+            }
+        }
+        for (int64_t e = d0 + tid + BK_T * BK_PFC; e < d1; e += BK_T) {   // longer rows
+            const double* row = e_new + (int64_t)a.mcol[e] * K;
+            const double mk = (double)mv[e];
+#pragma unroll
+            for (int c = 0; c < KT; ++c)
+                if (c < K) acc[c] = fma(mk, row[c], acc[c]);
+        }
+        const double tot = bk_reduce_scatter<KT>(acc, lane);
+        if ((lane & ((1 << SH) - 1)) == 0) s_part[wid][lane >> SH] = tot;
+        __syncthreads();
+        if (tid < K) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][tid];
+            const double dj = a.dinv[j];
+            const int64_t at = j * K + tid;
+            e_new[at] = identity ? e_old[at] - sum * dj : (r[at] - sum) * dj;
+        }
+        if (wid == 0) {
+            __syncwarp();
+            if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (blockIdx.x & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
+        }
+        __syncthreads();   // s_part is reused by the next row
+    }
+    if (tid == 0 && s_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+}
+
 // rho'_c = g_c^T z_c; the last block sets beta_c = rho'_c / rho_c (0 on the first call) and
 // rho_c = rho'_c for the active columns, and counts the preconditioner application
 __global__ void __launch_bounds__(BK_T) k_bk_gz(BkArgs a, int first) {
@@ -631,14 +723,22 @@ static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const doubl
 }
 
 // lane-per-column sweep for short rows, entry-parallel sweep (KT >= K accumulators) for long
+// mode 0: lane per column (short rows); 1: warp per row, lane per entry; 2: CTA per row
 template <typename MT, bool FWD>
-static const void* bk_sweep_kernel(bool ep, int K) {
-    if (!ep) return (const void*)k_bk_sweep<MT, FWD>;
-    if (K <= 2) return (const void*)k_bk_sweep_ep<MT, FWD, 2>;
-    if (K <= 4) return (const void*)k_bk_sweep_ep<MT, FWD, 4>;
-    if (K <= 8) return (const void*)k_bk_sweep_ep<MT, FWD, 8>;
-    if (K <= 16) return (const void*)k_bk_sweep_ep<MT, FWD, 16>;
-    return (const void*)k_bk_sweep_ep<MT, FWD, 32>;
+static const void* bk_sweep_kernel(int mode, int K) {
+    if (mode == 0) return (const void*)k_bk_sweep<MT, FWD>;
+    if (mode == 1) {
+        if (K <= 2) return (const void*)k_bk_sweep_ep<MT, FWD, 2>;
+        if (K <= 4) return (const void*)k_bk_sweep_ep<MT, FWD, 4>;
+        if (K <= 8) return (const void*)k_bk_sweep_ep<MT, FWD, 8>;
+        if (K <= 16) return (const void*)k_bk_sweep_ep<MT, FWD, 16>;
+        return (const void*)k_bk_sweep_ep<MT, FWD, 32>;
+    }
+    if (K <= 2) return (const void*)k_bk_sweep_cta<MT, FWD, 2>;
+    if (K <= 4) return (const void*)k_bk_sweep_cta<MT, FWD, 4>;
+    if (K <= 8) return (const void*)k_bk_sweep_cta<MT, FWD, 8>;
+    if (K <= 16) return (const void*)k_bk_sweep_cta<MT, FWD, 16>;
+    return (const void*)k_bk_sweep_cta<MT, FWD, 32>;
 }
 
 struct BkOut {
@@ -722,11 +822,13 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         else k_bk_cols<DT><<<gcols, BK_T, 0, st>>>(a, 0, dst);
         count_launch();
     };
-    // rows whose dependency side averages more than 24 entries take the entry-parallel sweep
-    const bool ep = (double)(SH->nnz_M - n) / (2.0 * (double)n) > 24.0;
+    // the sweep form follows the mean length of a row's dependency side: lane per column up to
+    // 24 entries, lane per entry up to 96, a CTA per row beyond
+    const double dep = (double)(SH->nnz_M - n) / (2.0 * (double)n);
+    const int smode = dep > 96.0 ? 2 : (dep > 24.0 ? 1 : 0);
     const bool m32 = P->op_dtype == LSQ_F32;
-    const void* kf = m32 ? bk_sweep_kernel<float, true>(ep, K) : bk_sweep_kernel<double, true>(ep, K);
-    const void* kb = m32 ? bk_sweep_kernel<float, false>(ep, K) : bk_sweep_kernel<double, false>(ep, K);
+    const void* kf = m32 ? bk_sweep_kernel<float, true>(smode, K) : bk_sweep_kernel<double, true>(smode, K);
+    const void* kb = m32 ? bk_sweep_kernel<float, false>(smode, K) : bk_sweep_kernel<double, false>(smode, K);
     lsq_status sweep_status = LSQ_OK;
     auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int idx) {
         lsq_status q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, st);

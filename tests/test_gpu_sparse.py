@@ -24,6 +24,7 @@ CASES = {
     "sprand": lambda: W.sparse_random(20000, 300, 8, 3),
     "graph": lambda: W.graph_incidence(2000, 9000, 4),
     "wide": lambda: W.sparse_random(60000, 2000, 8, 5),
+    "mid": lambda: W.sparse_random(30000, 3000, 4, 7),
 }
 
 
@@ -169,10 +170,11 @@ def test_sparse_block_f32_refinement(lsq, orc):
         assert info.converged[c] == 1 and info.relres_true[c] <= o.tol
 
 
-@pytest.mark.parametrize("case,k", [("sprand", 3), ("wide", 2)])
+@pytest.mark.parametrize("case,k", [("mid", 4), ("sprand", 3), ("wide", 2)])
 def test_sparse_block_long_rows_two_sweeps(lsq, orc, case, k):
-    """M rows of hundreds of entries take the entry-parallel block sweep; t = 2 also
-    exercises its other-side terms (the previous sweep's values)."""
+    """Rows of M with ~60 dependency entries take the lane-per-entry block sweep, rows of
+    hundreds take the CTA-per-row sweep; t = 2 also exercises their other-side terms (the
+    previous sweep's values)."""
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 313, sweeps=2)
     xs, b = W.rhs_for(seen, k, 1e-3, 31)
     X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)

@@ -454,8 +454,17 @@ static double dot(int64_t n, const double* a, const double* b) {
     return s;
 }
 
+/* z = P g: the SGS operator of Alg. 3 with t sweeps, or, for t = 0, the identity.  t = 0
+ * is the paper's comparison method of Sec. 5, CG on the column-normalised matrix
+ * (diagonally preconditioned CG); Alg. 3 itself would give the zero operator there. */
+static void precond_apply(const orc_M* M, int t, const double* g, double* z) {
+    if (t == 0) memcpy(z, g, (size_t)M->n * sizeof(double));
+    else orc_sgs_apply(M, t, g, z);
+}
+
 /* ------------------------------------------------------------------------------------
- * Alg. 2 step 4: PCG on Â^T Â y = h, with z = P g from orc_sgs_apply (t sweeps).
+ * Alg. 2 step 4: PCG on Â^T Â y = h, with z = P g from orc_sgs_apply (t sweeps; t = 0:
+ * P = I, the comparison method of Sec. 5).
  *
  * Least-squares form (b != NULL): h = Â^T b and the true residual is Â^T (b - Â y).
  * Normal-equation form (b == NULL, h given): the true residual is h - Â^T (Â y).
@@ -505,7 +514,7 @@ int orc_pcg(const orc_mat* A, const double* d, const orc_M* M, int sweeps, const
         if (gn <= tol * hnorm) { info->converged = 1; status = ORC_OK; break; }
         if (info->iters >= maxit) break;
         info->outer = outer + 1; /* PCG (re)starts that ran */
-        orc_sgs_apply(M, sweeps, g, z);
+        precond_apply(M, sweeps, g, z);
         for (int64_t j = 0; j < n; ++j) p[j] = z[j];
         double rho = dot(n, g, z);
         while (info->iters < maxit) {
@@ -518,7 +527,7 @@ int orc_pcg(const orc_mat* A, const double* d, const orc_M* M, int sweeps, const
             gn = sqrt(dot(n, g, g));
             info->relres_rec = gn / hnorm;
             if (gn <= tol * hnorm) break;
-            orc_sgs_apply(M, sweeps, g, z);
+            precond_apply(M, sweeps, g, z);
             double rho_new = dot(n, g, z);
             double beta = rho_new / rho;
             rho = rho_new;

@@ -356,6 +356,40 @@ def test_pcg_terminates_in_n_steps_when_well_conditioned(orc):
     assert e @ N @ e <= 1e-24 * (e0 @ N @ e0)
 
 
+def _three_eigenvalue_matrix(m=300, pairs=5, ident=4, c=0.6, seed=8):
+    """Unit-norm columns whose Gram matrix has exactly three distinct eigenvalues: an
+    orthonormal Q (m x n) times a block-diagonal B with 2 x 2 blocks of unit columns at
+    cosine c (eigenvalues 1 - c, 1 + c) and identity columns (eigenvalue 1)."""
+    n = 2 * pairs + ident
+    Q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((m, n)))
+    B = np.eye(n)
+    for k in range(pairs):
+        a = 2 * k
+        B[a:a + 2, a:a + 2] = [[1.0, c], [0.0, math.sqrt(1 - c * c)]]
+    return Q @ B
+
+
+def test_cg_baseline_terminates_in_three_steps(orc):
+    # t = 0: CG on the column-normalised matrix (the paper's comparison method).  With
+    # three distinct eigenvalues of A^T A, CG reaches the solution in exactly three steps
+    # in exact arithmetic (the Krylov space has dimension 3 for a generic right-hand side).
+    A = _three_eigenvalue_matrix()
+    mat = {"kind": "dense", "A": A}
+    assert np.allclose(np.linalg.norm(A, axis=0), 1.0)
+    ev = np.linalg.eigvalsh(A.T @ A)
+    assert len(np.unique(np.round(ev, 12))) == 3
+    b = np.random.default_rng(1).standard_normal(A.shape[0])
+    smp = orc.Sample(mat, seed=2)
+    Mo = orc.SampledM(smp)
+    y, info = orc.pcg(smp.mat, smp.d, Mo, b=b, tol=1e-10, maxit=50, max_outer=1, sweeps=0)
+    assert info["converged"] == 1 and info["iters"] == 3
+    x_ref = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.linalg.norm(y / smp.d - x_ref) <= 1e-12 * np.linalg.norm(x_ref)
+    # the sampled SGS preconditioner gives a different (preconditioned) iteration
+    _, info1 = orc.pcg(smp.mat, smp.d, Mo, b=b, tol=1e-10, maxit=50, max_outer=1, sweeps=1)
+    assert info1["converged"] == 1
+
+
 def test_pcg_iteration_count_zero_for_zero_rhs(orc):
     mat = W.gaussian_dense(100, 5, 1)
     S = orc.Solve(mat, np.zeros(100), seed=1)

@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--maxit", type=int, default=1000000)
     ap.add_argument("--inner-tol", type=float, default=0.0)
+    ap.add_argument("--sweeps", type=int, default=1,
+                    help="t of Alg. 3; 0 = the paper's comparison method (CG on the normalised A)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
@@ -175,7 +177,7 @@ def run_reference(args):
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"udv_dense_{args.m}x{args.n}_kappa{args.kappa:g}",
-                       "tol": args.tol, "sweeps": 1, "s": math.ceil(4 * args.n * math.log(args.n))},
+                       "tol": args.tol, "sweeps": args.sweeps, "s": math.ceil(4 * args.n * math.log(args.n))},
             "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle setup (sampling, A_s^T A_s, SGS) on the full matrix + "
                                        f"{args.cpu_iters} PCG iterations per step, extrapolated to "
@@ -221,7 +223,7 @@ def run_ours(args):
             return api.Matrix(A32, vals_f64=Asrc), A32
         pairs = api.lsq_split_f64(Asrc)
         return api.Matrix(pairs, f32x2=True, vals_f64=Asrc), pairs
-    o = api.opts(seed=1002 + rank, tol=args.tol, maxit=args.maxit, precond_dtype=pdt,
+    o = api.opts(seed=1002 + rank, tol=args.tol, maxit=args.maxit, precond_dtype=pdt, sweeps=args.sweeps,
                  inner_tol=args.inner_tol, max_outer=50)
     stream = torch.cuda.current_stream()
 
@@ -328,7 +330,7 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic",
                 "config": {"workload": f"udv_dense_{m}x{n}_kappa{args.kappa:g}", "m": m, "n": n,
-                           "kappa": args.kappa, "tol": args.tol, "sweeps": 1, "s": int(info.s),
+                           "kappa": args.kappa, "tol": args.tol, "sweeps": args.sweeps, "s": int(info.s),
                            "mode": args.mode, "l2": "inputs larger than L2 (A is %.2f GB)" % (m * n * es / 1e9),
                            "parallelism": f"replicas{world}"},
                 "clocks": ck, "gpu_launches": int(launches),
@@ -368,7 +370,7 @@ def run_sparse_workload(args):
     v64 = torch.from_numpy(mat["vals"]).cuda()
     vals = v64.float() if dt == "f32" else v64
     Mx = api.Matrix(row_ptr=rp, col_idx=ci, vals=vals, n=mat["n"], vals_f64=v64 if dt == "f32" else None)
-    o = api.opts(seed=1003, tol=args.tol, maxit=args.maxit, max_outer=50, inner_tol=args.inner_tol,
+    o = api.opts(seed=1003, tol=args.tol, maxit=args.maxit, max_outer=50, inner_tol=args.inner_tol, sweeps=args.sweeps,
                  precond_dtype=1 if dt == "f32" else 0)
     B = torch.from_numpy(b).cuda()
     X = None
@@ -396,7 +398,8 @@ def run_sparse_workload(args):
     line = {"metric": METRIC, "value": k / tot, "unit": "solves/s (right-hand sides)", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3, "higher_is_better": True,
             "dtype": dt + ("+f64" if dt == "f32" else ""), "data": "synthetic",
-            "config": {"workload": name, "m": int(mat["m"]), "n": int(mat["n"]), "k": k, "tol": args.tol},
+            "config": {"workload": name, "m": int(mat["m"]), "n": int(mat["n"]), "k": k, "tol": args.tol,
+                       "sweeps": args.sweeps},
             "phases": res}
     print(json.dumps(line), flush=True)
 
@@ -480,8 +483,10 @@ def run_batch_workload(args):
     # the same problems, one at a time, FP64 values (the plain GPU solve), solves only
     singles = []
     for i, (T, seen, B) in enumerate(keep):
-        A64 = torch.from_numpy(seen["A"]).cuda()
-        M64 = api.Matrix(A64)
+        m, n = seen["A"].shape
+        A64 = torch.zeros(m, n + (n & 1), dtype=torch.float64, device="cuda")   # 16-byte rows
+        A64[:, :n] = torch.from_numpy(seen["A"]).cuda()
+        M64 = api.Matrix(A64[:, :n])
         po = api.opts(seed=200 + i)
         idx, p, d = api.lsq_sample_rows(M64, po)
         singles.append((A64, M64, api.lsq_build_precond(M64, idx, p, d, po), B))

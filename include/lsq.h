@@ -85,7 +85,9 @@ typedef struct {
     double tol;            /* relative residual tolerance eps (Alg. 2 step 4); 1e-10 */
     int32_t maxit;         /* cap on PCG iterations over all outer steps; 1000000 */
     int32_t max_outer;     /* cap on PCG (re)starts from the true residual; 20 */
-    int32_t sweeps;        /* t of Alg. 3 (forward and backward sweeps each); 1 */
+    int32_t sweeps;        /* t of Alg. 3 (forward and backward sweeps each); 1.  0 selects
+                              the paper's comparison method (Sec. 5): CG on the
+                              column-normalised A, i.e. P = I */
     double sample_factor;  /* C in s = ceil(C n ln n) (Alg. 2 step 2); 4.0 */
     int32_t normalize;     /* Alg. 2 step 1 on (1) or off (0); 1 */
     int32_t precond_dtype; /* LSQ_F64 or LSQ_F32: storage/arithmetic of the SGS operator */

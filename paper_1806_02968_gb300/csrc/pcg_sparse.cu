@@ -287,6 +287,31 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
     if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
+// t = 0 (the comparison method, P = I): z = g, with the convergence check of the first sweep
+__global__ void __launch_bounds__(SP_T) k_sp_identity(SpArgs a, const double* r, double* e, int check, int nparts) {
+    __shared__ double sh[40];
+    __shared__ int s_stop;
+    if (a.S->done) return;
+    if (check) {
+        const double gg = sum_parts(a.part + a.rblk, nparts, sh);
+        if (threadIdx.x == 0) {
+            const double gn = sqrt(gg);
+            int stop = 0;
+            if (gn <= a.tol * a.S->hn || gn <= a.inner_tol * a.S->gstart) stop = 1;
+            if (a.S->iters >= a.maxit) stop = 1;
+            s_stop = stop;
+            if (blockIdx.x == 0) a.S->rec = gn / a.S->hn;
+        }
+        __syncthreads();
+        if (s_stop) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.S->done = 1;
+            return;
+        }
+    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x)
+        e[j] = r[j];
+}
+
 // rho' = g^T z; first: p = z, else beta = rho'/rho, p = z + beta p; pt = D^{-1} p; epoch++
 __global__ void __launch_bounds__(SP_T) k_sp_gz(SpArgs a) {
     __shared__ double sh[40];
@@ -463,6 +488,11 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     };
     // z = P g: t forward then t backward sweeps (the first may carry the convergence check)
     auto precond = [&](int check) {
+        if (P->sweeps == 0) {
+            k_sp_identity<<<gvec, SP_T, 0, st>>>(a, a.g, a.z, check, gvec);
+            count_launch();
+            return;
+        }
         const double* eold = nullptr;
         double* bufs[2] = {a.e0, a.e1};
         int cur = 0, idx = 0;
@@ -630,6 +660,11 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
     a.done_f = (unsigned long long*)(base + o_f); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     a.S = (SpState*)(base + o_S);
+    if (P->sweeps == 0) {
+        LSQ_CUDA(cudaMemcpyAsync(e, r, 8 * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
+        LSQ_CUDA(cudaStreamSynchronize(st));
+        return LSQ_OK;
+    }
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(a.S, 0, sizeof(SpState), st));
         LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));

@@ -836,6 +836,14 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     };
     // z = P g: t forward then t backward sweeps
     auto precond = [&]() {
+        if (P->sweeps == 0) {   // the comparison method: P = I
+            const cudaError_t ce = cudaMemcpyAsync(a.z, a.g, 8 * (size_t)nK, cudaMemcpyDeviceToDevice, st);
+            if (ce != cudaSuccess) {
+                set_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(ce));
+                sweep_status = LSQ_ERR_CUDA;
+            }
+            return;
+        }
         const double* eold = nullptr;
         double* bufs[2] = {a.e0, a.e1};
         int cur = 0, idx = 0;

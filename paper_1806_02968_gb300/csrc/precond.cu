@@ -91,6 +91,14 @@ __global__ void k_reduce_M(int64_t n, int splits, const double* part, double* M,
     }
 }
 
+// The identity operator (t = 0: CG on the column-normalised system, the paper's comparison
+// method in Sec. 5)
+template <typename OT>
+__global__ void k_identity_op(int64_t n, OT* op) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += (int64_t)gridDim.x * blockDim.x)
+        op[t] = (t / n == t % n) ? OT(1) : OT(0);
+}
+
 // Column j of the SGS operator: Alg. 3 on r = e_j from e = 0, t forward sweeps (rows
 // 0..n-1) then t backward sweeps (rows n-1..0), each the in-place Gauss-Seidel update
 // e_k <- (r_k - sum_{l != k} M_kl e_l) / M_kk (equal to e <- e + B^{-1}(r - M e) forward
@@ -188,7 +196,11 @@ static lsq_status build_dense(const lsq_matrix* A, const int32_t* idx, const dou
     const int wpb = 4;
     size_t smem = (size_t)wpb * n * sizeof(double);
     unsigned g = (unsigned)((n + wpb - 1) / wpb);
-    if (H->op_dtype == LSQ_F32) {
+    if (H->sweeps == 0) {   // the comparison method: P = I on the normalised system
+        const unsigned gi = (unsigned)std::min<int64_t>((n * n + 255) / 256, 152 * 16);
+        if (H->op_dtype == LSQ_F32) k_identity_op<float><<<gi, 256, 0, st>>>(n, (float*)H->op);
+        else k_identity_op<double><<<gi, 256, 0, st>>>(n, (double*)H->op);
+    } else if (H->op_dtype == LSQ_F32) {
         if (smem > 48 * 1024)
             LSQ_CUDA(cudaFuncSetAttribute(k_sgs_materialize<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_sgs_materialize<float><<<g, 32 * wpb, smem, st>>>(n, H->sweeps, H->M, (float*)H->op);
@@ -229,7 +241,7 @@ extern "C" lsq_status lsq_build_precond(const lsq_matrix* A, const int32_t* idx,
     if (st0 != LSQ_OK) return st0;
     LSQ_CHECK_ARG(o && P_out && idx && p && colscale, "NULL argument");
     LSQ_CHECK_ARG(s > 0, "s must be positive");
-    LSQ_CHECK_ARG(o->sweeps >= 1 && o->sweeps <= 64, "sweeps must be in [1, 64]");
+    LSQ_CHECK_ARG(o->sweeps >= 0 && o->sweeps <= 64, "sweeps must be in [0, 64]");
     LSQ_CHECK_ARG(o->precond_dtype == LSQ_F64 || o->precond_dtype == LSQ_F32, "precond_dtype must be F64 or F32");
     *P_out = nullptr;
     if (A->dense) LSQ_CHECK_ARG(A->n <= 2048, "dense path supports n <= 2048");

@@ -206,3 +206,20 @@ def test_pcg_double_float_storage(lsq, orc, with_f64):
     # roundoff 2^-48) land closer than that.  Both are held to 12%.
     assert abs(int(info64.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info64.iters[0], oi["iters"])
     assert abs(int(info.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info.iters[0], oi["iters"])
+
+
+@pytest.mark.parametrize("gen", ["gauss", "udv"])
+def test_cg_baseline_dense_matches_oracle(lsq, orc, gen):
+    """sweeps = 0: the paper's comparison method (CG on the column-normalised A)."""
+    mat = {"gauss": lambda: W.gaussian_dense(4096, 128, 1001),
+           "udv": lambda: W.udv_dense(8192, 64, 1e2, 3)}[gen]()
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 21, sweeps=0)
+    xs, b = W.rhs_for(seen, 2, 1e-3, 22)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    kappa = np.linalg.cond(seen["A"] / smp.d)
+    for c in range(2):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=0)
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.05 * oi["iters"])

@@ -186,3 +186,23 @@ def test_sparse_block_long_rows_two_sweeps(lsq, orc, case, k):
         assert info.converged[c] == 1 and oi["converged"] == 1
         assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
         assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_sparse_cg_baseline_matches_oracle(lsq, orc, k):
+    """sweeps = 0 (CG on the column-normalised A) through the one-column path (k = 1) and
+    the block path (k = 3)."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["sprand"](), 77, sweeps=0)
+    xs, b = W.rhs_for(seen, k, 1e-3, 78)
+    B = torch.from_numpy(b if k > 1 else b[0]).cuda()
+    X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    X = X.cpu().numpy().reshape(k, -1)
+    A = W.dense_from_csr(seen)
+    kappa = np.linalg.cond(A / smp.d)
+    for c in range(k):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=0)
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.05 * oi["iters"])
+    r = torch.from_numpy(np.random.default_rng(0).standard_normal((2, seen["n"]))).cuda()
+    assert torch.equal(P.apply(r), r)

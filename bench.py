@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
-    ap.add_argument("--workload", choices=["udv", "sparse", "graph", "adjoint", "batch"], default="udv",
+    ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch"], default="udv",
                     help="udv: the timed benchmark; the others measure the CSR configurations")
     return ap.parse_args()
 
@@ -113,9 +113,19 @@ def make_problem(args, seed_base, device_matmul=True):
         import torch
         mm = lambda X, Y: (torch.from_numpy(np.ascontiguousarray(X)).cuda()
                            @ torch.from_numpy(np.ascontiguousarray(Y)).cuda()).cpu().numpy()
+    if args.workload == "gauss":   # Gaussian A (Sec. 5.1), b = A x* + 1e-3 noise
+        mat = W.gaussian_dense(args.m, args.n, seed_base)
+        xs, b = W.rhs_for(mat, 1, 1e-3, seed_base + 100)
+        return mat, xs[0], b[0]
     mat = W.udv_dense(args.m, args.n, args.kappa, seed_base, matmul=mm)
     xs, b = W.rhs_for(mat, 1, 1e-6, seed_base + 100)
     return mat, xs[0], b[0]
+
+
+def workload_name(args, m, n):
+    if args.workload == "gauss":
+        return f"gaussian_dense_{m}x{n}"
+    return f"udv_dense_{m}x{n}_kappa{args.kappa:g}"
 
 
 def peaks():
@@ -176,7 +186,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"udv_dense_{args.m}x{args.n}_kappa{args.kappa:g}",
+            "config": {"workload": workload_name(args, args.m, args.n),
                        "tol": args.tol, "sweeps": args.sweeps, "s": math.ceil(4 * args.n * math.log(args.n))},
             "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle setup (sampling, A_s^T A_s, SGS) on the full matrix + "
@@ -329,7 +339,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic",
-                "config": {"workload": f"udv_dense_{m}x{n}_kappa{args.kappa:g}", "m": m, "n": n,
+                "config": {"workload": workload_name(args, m, n), "m": m, "n": n,
                            "kappa": args.kappa, "tol": args.tol, "sweeps": args.sweeps, "s": int(info.s),
                            "mode": args.mode, "l2": "inputs larger than L2 (A is %.2f GB)" % (m * n * es / 1e9),
                            "parallelism": f"replicas{world}"},
@@ -529,7 +539,7 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch_workload(args)
-    elif args.workload != "udv":
+    elif args.workload not in ("udv", "gauss"):
         run_sparse_workload(args)
     else:
         run_ours(args)

@@ -249,7 +249,16 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (v >= target) break;
-                if (++polls > (1u << 22)) { ok = false; break; }
+                // one failed wait ends them all: it sets the error word, which every wait
+                // checks while polling
+                ++polls;
+                const bool give_up = polls > (1u << 22) ||
+                                     ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u);
+                if (__any_sync(0xffffffffu, give_up)) {
+                    ok = false;
+                    if (lane == 0) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+                    break;
+                }
                 if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
             }
             // each lane acquired one sub-counter; the warp barrier orders every lane's loads

@@ -285,8 +285,10 @@ __global__ void __launch_bounds__(BK_T) k_bk_update(BkArgs a) {
 // Wait until every row of level L-1 has finished the current sweep: the 32 completion
 // sub-counters of that level (separate cache lines), one per lane, summed by the warp
 // (acquire loads, bounded polls with exponential backoff).
+// A wait that gives up sets DEV_ERR_TIMEOUT in *err at once, and every wait checks *err while
+// polling, so one failure ends all waits of the launch instead of each running to its bound.
 __device__ __forceinline__ bool bk_level_wait(const unsigned long long* done, int L, unsigned long long epoch,
-                                              const int64_t* lsz, int lane) {
+                                              const int64_t* lsz, int lane, unsigned* err) {
     if (L == 0) return true;
     const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
     const unsigned long long* cntp = done + (int64_t)(L - 1) * LVL_WORDS;
@@ -297,7 +299,13 @@ __device__ __forceinline__ bool bk_level_wait(const unsigned long long* done, in
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (v >= target) break;
-        if (++polls > (1u << 22)) { ok = false; break; }
+        ++polls;
+        const bool give_up = polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u);
+        if (__any_sync(0xffffffffu, give_up)) {
+            ok = false;
+            if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+            break;
+        }
         if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
     }
     __syncwarp();
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
             pm[c] = 0.0;
             if (e < d1) { pk[c] = a.mcol[e]; pm[c] = (double)mv[e]; }
         }
-        ok = bk_level_wait(done, L, epoch, lsz, lane) && ok;
+        ok = bk_level_wait(done, L, epoch, lsz, lane, &a.S->err) && ok;
 #pragma unroll
         for (int c = 0; c < BK_PF; ++c) {
             const int64_t cbase = d0 + 32 * c;
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r,
             pm[u] = 0.0;
             if (e < d1) { pk[u] = a.mcol[e]; pm[u] = (double)mv[e]; }
         }
-        ok = bk_level_wait(done, L, epoch, lsz, lane) && ok;
+        ok = bk_level_wait(done, L, epoch, lsz, lane, &a.S->err) && ok;
 #pragma unroll
         for (int u = 0; u < BK_PFE; ++u) {
             if (pk[u] >= 0) {
@@ -550,7 +558,7 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r
             if (e < d1) { pk[u] = a.mcol[e]; pm[u] = (double)mv[e]; }
         }
         if (wid == 0) {
-            const bool ok = bk_level_wait(done, L, epoch, lsz, lane);
+            const bool ok = bk_level_wait(done, L, epoch, lsz, lane, &a.S->err);
             if (!ok && lane == 0) s_bad = 1;
             __threadfence();
         }

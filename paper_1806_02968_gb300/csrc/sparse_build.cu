@@ -393,48 +393,121 @@ __global__ void k_to_f32(const double* src, float* dst, int64_t count) {
         dst[e] = (float)src[e];
 }
 
-// Level schedule on the host: lev_f(j) = 1 + max lev_f(k) over k < j with M_jk != 0 (rows in
-// natural order), lev_b(j) = 1 + max lev_b(k) over k > j (rows in reverse order); each
-// schedule lists the rows by level, then by row index, with the level of every slot and the
-// number of rows of every level.
-struct Levels {
-    std::vector<int32_t> sched, lvl;
-    std::vector<int64_t> size;
-};
-static void host_levels(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                        Levels& F, Levels& B) {
-    std::vector<int32_t> lf(n, 0), lb(n, 0);
-    int32_t mf = 0, mb = 0;
-    for (int64_t j = 0; j < n; ++j) {
-        int32_t l = 0;
-        for (int64_t e = rp[j]; e < rp[j + 1]; ++e)
-            if (ci[e] < j) l = std::max(l, lf[ci[e]] + 1);
-        lf[j] = l;
-        mf = std::max(mf, l);
-    }
-    for (int64_t j = n - 1; j >= 0; --j) {
-        int32_t l = 0;
-        for (int64_t e = rp[j]; e < rp[j + 1]; ++e)
-            if (ci[e] > j) l = std::max(l, lb[ci[e]] + 1);
-        lb[j] = l;
-        mb = std::max(mb, l);
-    }
-    auto order = [n](const std::vector<int32_t>& lev, int32_t maxl, Levels& out) {
-        std::vector<int64_t> c(maxl + 2, 0);
-        for (int64_t j = 0; j < n; ++j) c[lev[j] + 1]++;
-        out.size.assign(maxl + 1, 0);
-        for (int32_t l = 0; l <= maxl; ++l) out.size[l] = c[l + 1];
-        for (int32_t l = 0; l <= maxl; ++l) c[l + 1] += c[l];
-        out.sched.assign(n, 0);
-        out.lvl.assign(n, 0);
-        for (int64_t j = 0; j < n; ++j) {
-            const int64_t at = c[lev[j]]++;
-            out.sched[at] = (int32_t)j;
-            out.lvl[at] = lev[j];
+// Level schedules: lev_f(j) = 1 + max lev_f(k) over k < j with M_jk != 0 (rows in natural
+// order), lev_b(j) = 1 + max lev_b(k) over k > j (reverse order), 0 for a row without such
+// entries.  Each schedule lists the rows by level (any order inside a level: those rows are
+// independent) with the level of every slot and the number of rows of every level.
+//
+// k_levels: cooperative launch; warp w takes rows w, w + W, ... in dependency order (natural
+// order forward, reverse backward), so every row a row depends on is taken by a warp no later
+// than the row itself and, every warp being resident, every wait ends.  lev1 holds level + 1
+// (0 = not yet known).  Waits are bounded; one failed wait sets *err and ends them all.
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_levels(int64_t n, const int64_t* mptr, const int32_t* mcol,
+                                                const int64_t* mdiag, int* lev1, int* maxlev, unsigned* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int mymax = 0;
+    for (int64_t t = gw; t < n; t += W) {
+        const int64_t j = FWD ? t : n - 1 - t;
+        const int64_t d0 = FWD ? mptr[j] : mdiag[j] + 1, d1 = FWD ? mdiag[j] : mptr[j + 1];
+        int mx = 0;
+        for (int64_t e = d0 + lane; e < d1; e += 32) {
+            const int32_t k = mcol[e];
+            int v = ld_acquire_i32(lev1 + k);
+            unsigned polls = 0, ns = 32;
+            while (v == 0) {
+                ++polls;
+                if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    v = 1;
+                    break;
+                }
+                if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+                v = ld_acquire_i32(lev1 + k);
+            }
+            mx = max(mx, v);
         }
-    };
-    order(lf, mf, F);
-    order(lb, mb, B);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) st_release_i32(lev1 + j, mx + 1);   // level(j) = mx, stored + 1
+        mymax = max(mymax, mx);
+    }
+    if (lane == 0) atomicMax(maxlev, mymax);
+}
+// rows per level, from lev1 (level + 1)
+__global__ void k_level_count(int64_t n, const int* lev1, unsigned long long* cnt) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + (lev1[j] - 1), 1ull);
+}
+// slot of every row: its level's offset plus a cursor (order inside a level is free)
+__global__ void k_level_scatter(int64_t n, const int* lev1, const int64_t* off, unsigned long long* cur,
+                                int32_t* sched, int32_t* lvl) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lev1[j] - 1;
+        const int64_t at = off[l] + (int64_t)atomicAdd(cur + l, 1ull);
+        sched[at] = (int32_t)j;
+        lvl[at] = l;
+    }
+}
+
+// One direction's schedule on the device: sched (n), lvl (n), lsize (levels), nlev.
+template <bool FWD>
+static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sched, int32_t** lvl, int64_t** lsize,
+                                int64_t* nlev, cudaStream_t st) {
+    int dev = 0, sms = 0, per = 0;
+    LSQ_CUDA(cudaGetDevice(&dev));
+    LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_levels<FWD>, 256, 0));
+    if (per < 1) { set_error("level kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
+    Scratch sc;
+    LSQ_CUDA(sc.alloc(4 * (size_t)n + 256, st));
+    int* lev1 = sc.as<int>();
+    int* maxlev = lev1 + n;
+    unsigned* err = reinterpret_cast<unsigned*>(maxlev + 1);
+    LSQ_CUDA(cudaMemsetAsync(lev1, 0, 4 * (size_t)n + 256, st));
+    int64_t nn = n;
+    const int64_t* mptr = S->mptr;
+    const int32_t* mcol = S->mcol;
+    const int64_t* mdiag = S->mdiag;
+    void* params[] = {&nn, (void*)&mptr, (void*)&mcol, (void*)&mdiag, &lev1, &maxlev, &err};
+    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)k_levels<FWD>, dim3(sms * per), dim3(256), params, 0, st));
+    count_launch();
+    int hmax[2] = {0, 0};
+    LSQ_CUDA(cudaMemcpyAsync(hmax, maxlev, 8, cudaMemcpyDeviceToHost, st));
+    LSQ_CUDA(cudaStreamSynchronize(st));
+    if (hmax[1] != 0) { set_error("level schedule: a dependency wait timed out"); return LSQ_ERR_TIMEOUT; }
+    const int64_t L = (int64_t)hmax[0] + 1;
+    LSQ_CUDA(cudaMalloc(sched, 4 * (size_t)n));
+    LSQ_CUDA(cudaMalloc(lvl, 4 * (size_t)n));
+    LSQ_CUDA(cudaMalloc(lsize, 8 * (size_t)L));
+    Scratch sc2;
+    const int64_t nt = (L + SC_T - 1) / SC_T;   // scan_i64: out[0..L], ceil(L / 512) scratch
+    LSQ_CUDA(sc2.alloc(8 * (size_t)((L + 1) + L + nt + 1), st));
+    int64_t* off = sc2.as<int64_t>();
+    unsigned long long* cur = reinterpret_cast<unsigned long long*>(off + L + 1);
+    int64_t* scan_scratch = off + (L + 1) + L;
+    LSQ_CUDA(cudaMemsetAsync(*lsize, 0, 8 * (size_t)L, st));
+    LSQ_CUDA(cudaMemsetAsync(cur, 0, 8 * (size_t)L, st));
+    k_level_count<<<grid1(n), 256, 0, st>>>(n, lev1, reinterpret_cast<unsigned long long*>(*lsize));
+    count_launch();
+    lsq_status r = scan_i64(*lsize, L, off, scan_scratch, st);
+    if (r != LSQ_OK) return r;
+    k_level_scatter<<<grid1(n), 256, 0, st>>>(n, lev1, off, cur, *sched, *lvl);
+    count_launch();
+    LSQ_CUDA(cudaGetLastError());
+    LSQ_CUDA(cudaStreamSynchronize(st));
+    *nlev = L;
+    return LSQ_OK;
 }
 
 lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p, int64_t s,
@@ -545,28 +618,12 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
     unsigned long long nf = 0;
     LSQ_CUDA(cudaMemcpyAsync(&nf, nfix, 8, cudaMemcpyDeviceToHost, st));
     LSQ_CUDA(cudaGetLastError());
-    // 4. level schedules (host) from M's pattern
-    std::vector<int64_t> hrp(n + 1);
-    std::vector<int32_t> hci(mnnz);
-    LSQ_CUDA(cudaMemcpyAsync(hrp.data(), S->mptr, 8 * (size_t)(n + 1), cudaMemcpyDeviceToHost, st));
-    LSQ_CUDA(cudaMemcpyAsync(hci.data(), S->mcol, 4 * (size_t)mnnz, cudaMemcpyDeviceToHost, st));
     LSQ_CUDA(cudaStreamSynchronize(st));
-    Levels LF, LB;
-    host_levels(n, hrp, hci, LF, LB);
-    S->nlev_f = (int64_t)LF.size.size();
-    S->nlev_b = (int64_t)LB.size.size();
-    LSQ_CUDA(cudaMalloc(&S->sched_f, 4 * (size_t)n));
-    LSQ_CUDA(cudaMalloc(&S->sched_b, 4 * (size_t)n));
-    LSQ_CUDA(cudaMalloc(&S->lvl_f, 4 * (size_t)n));
-    LSQ_CUDA(cudaMalloc(&S->lvl_b, 4 * (size_t)n));
-    LSQ_CUDA(cudaMalloc(&S->lsize_f, 8 * (size_t)S->nlev_f));
-    LSQ_CUDA(cudaMalloc(&S->lsize_b, 8 * (size_t)S->nlev_b));
-    LSQ_CUDA(cudaMemcpyAsync(S->sched_f, LF.sched.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
-    LSQ_CUDA(cudaMemcpyAsync(S->sched_b, LB.sched.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
-    LSQ_CUDA(cudaMemcpyAsync(S->lvl_f, LF.lvl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
-    LSQ_CUDA(cudaMemcpyAsync(S->lvl_b, LB.lvl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
-    LSQ_CUDA(cudaMemcpyAsync(S->lsize_f, LF.size.data(), 8 * (size_t)S->nlev_f, cudaMemcpyHostToDevice, st));
-    LSQ_CUDA(cudaMemcpyAsync(S->lsize_b, LB.size.data(), 8 * (size_t)S->nlev_b, cudaMemcpyHostToDevice, st));
+    // 4. level schedules of the forward and backward sweeps (device)
+    r = device_levels<true>(S, n, &S->sched_f, &S->lvl_f, &S->lsize_f, &S->nlev_f, st);
+    if (r != LSQ_OK) return r;
+    r = device_levels<false>(S, n, &S->sched_b, &S->lvl_b, &S->lsize_b, &S->nlev_b, st);
+    if (r != LSQ_OK) return r;
     // 5. transposed pattern of A for the A^T q pass (values are gathered at solve time)
     LSQ_CUDA(cudaMalloc(&S->atptr, 8 * (size_t)(n + 1)));
     LSQ_CUDA(cudaMalloc(&S->atrow, 4 * (size_t)A->nnz));

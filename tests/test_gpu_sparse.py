@@ -63,7 +63,14 @@ def test_sparse_pcg_matches_oracle(lsq, orc, case, noise):
         assert info.relres_true[c] <= o.tol
         assert rel(X[c], x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
         assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info.iters[c], oi["iters"])
-    assert info.levels >= 1 and info.nnz_M == Mo.val.size
+    assert info.nnz_M == Mo.val.size
+    # forward level count of Alg. 3's dependency DAG, computed here from M's pattern
+    lev = np.zeros(seen["n"], np.int64)
+    for j in range(seen["n"]):
+        cols = Mo.col[Mo.row_ptr[j]:Mo.row_ptr[j + 1]]
+        dep = cols[cols < j]
+        lev[j] = 1 + lev[dep].max() if dep.size else 0
+    assert info.levels == lev.max() + 1
 
 
 def test_sparse_f32_values_with_f64_refinement(lsq, orc):

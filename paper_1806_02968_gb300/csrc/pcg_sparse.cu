@@ -46,6 +46,9 @@ struct SpArgs {
     const int32_t* sched_f;
     const int32_t* sched_b;
     const int32_t* lvl_f;       // level of each schedule slot
+    const int64_t* loff_f;      // first slot of each level
+    const int64_t* loff_b;
+    int64_t one_f, one_b;       // level count when that direction runs in one CTA, else 0
     const int32_t* lvl_b;
     const int64_t* lsize_f;     // rows per level
     const int64_t* lsize_b;
@@ -296,6 +299,108 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
     if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
+// The same sweep in ONE CTA, for deep and narrow level structures (few rows per level): the
+// levels follow one another at block barriers instead of completion counters.  Warp w takes
+// rows w, w + NW, ... of each level; the indices and values of its first row of the next level
+// (which do not depend on this sweep's values) are loaded before the barrier, so after it only
+// the gathers of e_new stand between two levels.
+constexpr int S1_T = 512;
+template <typename MT, bool FWD>
+__global__ void __launch_bounds__(S1_T, 1) k_sp_sweep_1cta(SpArgs a, const double* r, const double* e_old,
+                                                           double* e_new, int identity, int check, int nparts,
+                                                           int64_t nlev) {
+    __shared__ double sh[40];
+    __shared__ int s_stop;
+    if (a.S->done) return;
+    if (check) {
+        const double gg = sum_parts(a.part + a.rblk, nparts, sh);
+        if (threadIdx.x == 0) {
+            const double gn = sqrt(gg);
+            int stop = 0;
+            if (gn <= a.tol * a.S->hn || gn <= a.inner_tol * a.S->gstart) stop = 1;
+            if (a.S->iters >= a.maxit) stop = 1;
+            s_stop = stop;
+            a.S->rec = gn / a.S->hn;
+            if (stop) a.S->done = 1;
+        }
+        __syncthreads();
+        if (s_stop) return;
+    }
+    const int32_t* sched = FWD ? a.sched_f : a.sched_b;
+    const int64_t* loff = FWD ? a.loff_f : a.loff_b;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = S1_T / 32;
+    const bool other = !identity && e_old != nullptr;
+    // one row's inputs that do not depend on this sweep
+    struct Row {
+        int64_t j, d0, d1;
+        double base;        // r_j (or e_old_j for the identity form)
+        double acc;         // this lane's other-side terms
+        int32_t kk[SW_PF];
+        double mm[SW_PF];
+    };
+    auto load_row = [&](int64_t j, Row& R) {
+        R.j = j;
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        R.d0 = FWD ? e0 : ed + 1;
+        R.d1 = FWD ? ed : e1;
+        const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
+        R.base = identity ? e_old[j] : r[j];
+        R.acc = 0.0;
+        if (other)
+            for (int64_t e = o0 + lane; e < o1; e += 32) R.acc = fma((double)mv[e], e_old[a.mcol[e]], R.acc);
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c) {
+            const int64_t e = R.d0 + lane + 32 * c;
+            R.kk[c] = -1;
+            R.mm[c] = 0.0;
+            if (e < R.d1) { R.kk[c] = a.mcol[e]; R.mm[c] = (double)mv[e]; }
+        }
+    };
+    auto finish_row = [&](const Row& R) {
+        double acc = R.acc;
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c)
+            if (R.kk[c] >= 0) acc = fma(R.mm[c], e_new[R.kk[c]], acc);
+        for (int64_t base = R.d0 + 32 * SW_PF; base < R.d1; base += 32 * 8) {
+            int32_t k2[8];
+            double m2[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t e = base + lane + 32 * u;
+                k2[u] = -1;
+                m2[u] = 0.0;
+                if (e < R.d1) { k2[u] = a.mcol[e]; m2[u] = (double)mv[e]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k2[u] >= 0) acc = fma(m2[u], e_new[k2[u]], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double dj = a.dinv[R.j];
+            e_new[R.j] = identity ? R.base - acc * dj : (R.base - acc) * dj;
+        }
+    };
+    Row cur;
+    int64_t lo = loff[0], hi = loff[1];
+    if (w < hi - lo) load_row(sched[lo + w], cur);
+    for (int64_t L = 0; L < nlev; ++L) {
+        const int64_t cnt = hi - lo;
+        for (int64_t q = w; q < cnt; q += NW) {
+            if (q != w) load_row(sched[lo + q], cur);
+            finish_row(cur);
+        }
+        if (L + 1 < nlev) {
+            lo = hi;
+            hi = loff[L + 2];
+            if (w < hi - lo) load_row(sched[lo + w], cur);
+        }
+        __syncthreads();   // this level's values are visible to every warp
+    }
+}
+
 // t = 0 (the comparison method, P = I): z = g, with the convergence check of the first sweep
 __global__ void __launch_bounds__(SP_T) k_sp_identity(SpArgs a, const double* r, double* e, int check, int nparts) {
     __shared__ double sh[40];
@@ -406,11 +511,25 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
         if (per < 1) { set_error("sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
         grid = sms * per;
     }
+    const int64_t nl = FWD ? a.one_f : a.one_b;
+    if (nl > 0) {   // deep, narrow level structure: the whole sweep in one CTA
+        k_sp_sweep_1cta<MT, FWD><<<1, S1_T, 0, st>>>(a, r, eold, enew, identity, check, nparts, nl);
+        count_launch();
+        LSQ_CUDA(cudaGetLastError());
+        return LSQ_OK;
+    }
     SpArgs av = a;
     void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &check, &nparts, &idx};
     LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(SP_T), params, 0, st));
     count_launch();
     return LSQ_OK;
+}
+
+// One CTA per sweep when levels hold fewer than 256 rows on average: block barriers between
+// levels are then cheaper than a grid of warps waiting on completion counters.
+static void choose_sweep_form(SpArgs& a, const SparseHandle* SH, int64_t n) {
+    a.one_f = SH->nlev_f * 256 > n ? SH->nlev_f : 0;
+    a.one_b = SH->nlev_b * 256 > n ? SH->nlev_b : 0;
 }
 
 static unsigned gridn(int64_t work, int64_t cap = 152 * 8) {
@@ -455,7 +574,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.w = vec + 5 * n; a.e0 = vec + 6 * n; a.e1 = vec + 7 * n; a.h = vec + 8 * n;
     double* tmpv = vec + 9 * n;
     a.q = (double*)(base + o_q);
-    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
+    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n); a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
     a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     auto lanes_for = [](double mean) { int L = 1; while (L < 32 && L < mean) L <<= 1; return L; };
     a.lpr = lanes_for((double)nnz / (double)m);
@@ -666,7 +785,7 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b; a.sweeps = P->sweeps;
     a.e0 = (double*)(base + o_e); a.e1 = a.e0 + n;
-    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
+    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n); a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
     a.done_f = (unsigned long long*)(base + o_f); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     a.S = (SpState*)(base + o_S);
     if (P->sweeps == 0) {

@@ -21,6 +21,8 @@ struct SparseHandle {
     int64_t* lsize_f = nullptr;   // rows per level
     int64_t* lsize_b = nullptr;
     int64_t nlev_f = 0, nlev_b = 0;
+    int64_t* loff_f = nullptr;    // first schedule slot of every level (nlev + 1 entries)
+    int64_t* loff_b = nullptr;
     // transposed pattern of A: column pointers, row indices, source entry of each
     int64_t* atptr = nullptr;
     int32_t* atrow = nullptr;

@@ -463,7 +463,7 @@ __global__ void k_level_scatter(int64_t n, const int* lev1, const int64_t* off, 
 // One direction's schedule on the device: sched (n), lvl (n), lsize (levels), nlev.
 template <bool FWD>
 static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sched, int32_t** lvl, int64_t** lsize,
-                                int64_t* nlev, cudaStream_t st) {
+                                int64_t** loff, int64_t* nlev, cudaStream_t st) {
     int dev = 0, sms = 0, per = 0;
     LSQ_CUDA(cudaGetDevice(&dev));
     LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -504,6 +504,8 @@ static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sche
     if (r != LSQ_OK) return r;
     k_level_scatter<<<grid1(n), 256, 0, st>>>(n, lev1, off, cur, *sched, *lvl);
     count_launch();
+    LSQ_CUDA(cudaMalloc(loff, 8 * (size_t)(L + 1)));
+    LSQ_CUDA(cudaMemcpyAsync(*loff, off, 8 * (size_t)(L + 1), cudaMemcpyDeviceToDevice, st));
     LSQ_CUDA(cudaGetLastError());
     LSQ_CUDA(cudaStreamSynchronize(st));
     *nlev = L;
@@ -620,9 +622,9 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
     LSQ_CUDA(cudaGetLastError());
     LSQ_CUDA(cudaStreamSynchronize(st));
     // 4. level schedules of the forward and backward sweeps (device)
-    r = device_levels<true>(S, n, &S->sched_f, &S->lvl_f, &S->lsize_f, &S->nlev_f, st);
+    r = device_levels<true>(S, n, &S->sched_f, &S->lvl_f, &S->lsize_f, &S->loff_f, &S->nlev_f, st);
     if (r != LSQ_OK) return r;
-    r = device_levels<false>(S, n, &S->sched_b, &S->lvl_b, &S->lsize_b, &S->nlev_b, st);
+    r = device_levels<false>(S, n, &S->sched_b, &S->lvl_b, &S->lsize_b, &S->loff_b, &S->nlev_b, st);
     if (r != LSQ_OK) return r;
     // 5. transposed pattern of A for the A^T q pass (values are gathered at solve time)
     LSQ_CUDA(cudaMalloc(&S->atptr, 8 * (size_t)(n + 1)));
@@ -646,7 +648,7 @@ void free_sparse(SparseHandle* S) {
     cudaFree(S->mptr); cudaFree(S->mcol); cudaFree(S->mval); cudaFree(S->mval32); cudaFree(S->dinv); cudaFree(S->mdiag);
     cudaFree(S->sched_f); cudaFree(S->sched_b); cudaFree(S->lvl_f); cudaFree(S->lvl_b);
     cudaFree(S->lsize_f); cudaFree(S->lsize_b); cudaFree(S->atptr); cudaFree(S->atrow);
-    cudaFree(S->atperm);
+    cudaFree(S->atperm); cudaFree(S->loff_f); cudaFree(S->loff_b);
     delete S;
 }
 

@@ -25,6 +25,8 @@ CASES = {
     "graph": lambda: W.graph_incidence(2000, 9000, 4),
     "wide": lambda: W.sparse_random(60000, 2000, 8, 5),
     "mid": lambda: W.sparse_random(30000, 3000, 4, 7),
+    # wide levels (~1000 rows each): the sweeps run on the whole grid, not in one CTA
+    "graph_wide": lambda: W.graph_incidence(20000, 90000, 4),
 }
 
 
@@ -38,7 +40,7 @@ def test_sparse_normal_matrix_pattern_and_values(lsq, orc, case):
 
 
 @pytest.mark.parametrize("sweeps", [1, 2])
-@pytest.mark.parametrize("case", ["sprand", "graph", "wide"])
+@pytest.mark.parametrize("case", ["sprand", "graph", "wide", "graph_wide"])
 def test_sparse_sweeps_match_alg3(lsq, orc, case, sweeps):
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003, sweeps=sweeps)
     rng = np.random.default_rng(sweeps)
@@ -48,7 +50,7 @@ def test_sparse_sweeps_match_alg3(lsq, orc, case, sweeps):
         assert rel(E[c], orc.sgs_apply(Mo, R[c], sweeps)) <= 1e-11
 
 
-@pytest.mark.parametrize("case,noise", [("sprand", 1e-3), ("graph", 1e-4)])
+@pytest.mark.parametrize("case,noise", [("sprand", 1e-3), ("graph", 1e-4), ("graph_wide", 1e-4)])
 def test_sparse_pcg_matches_oracle(lsq, orc, case, noise):
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003)
     xs, b = W.rhs_for(seen, 2, noise, 17)
@@ -101,7 +103,7 @@ def test_sparse_adjoint_matches_oracle(lsq, orc):
     assert rel(gv.cpu().numpy(), gsum) <= 1e-8
 
 
-@pytest.mark.parametrize("case", ["sprand", "graph"])
+@pytest.mark.parametrize("case", ["sprand", "graph", "graph_wide"])
 def test_sparse_pcg_single_column_matches_oracle(lsq, orc, case):
     """k = 1 runs the one-column path (lanes per row of A; scalar recurrences)."""
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 2029)

@@ -14,11 +14,13 @@
 //              ||g||^2; the masks; z = (materialised SGS operator) g on the slice; rho', beta,
 //              p, and the next P~ broadcast into every CTA's shared memory
 // The inner iteration runs in FP32 (products and the W accumulation); all vectors, dots and
-// scalars are FP64.  Restarts (outer steps) recompute g from the FP64 residual
-// D^{-1} A^T (b - A x) with FP64 arithmetic on the same values, which also refines x.
+// scalars are FP64.  Restarts (outer steps) recompute g from the residual D^{-1} A^T (b - A x)
+// in double-float on the FP32 units (about 48 bits; A's values are exact in FP32), which also
+// refines x.
 // Every decision (alpha, masks, loop exits) is computed identically by all CTAs of a cluster
 // from the same sums in the same order, so their control flow cannot diverge.
 #include "batch.cuh"
+#include "dfloat.cuh"
 
 #include <cooperative_groups.h>
 
@@ -190,6 +192,126 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
     __syncthreads();
 }
 
+// The FP64-accurate residual pass in double-float on the FP32 units (A's values are exact
+// in FP32; x and q are (hi, lo) float pairs; products and sums follow the cascaded Dot2 form
+// of Ogita, Rump & Oishi):  Q = b - A X, Wp = A^T Q over rows [r_lo, r_hi) (pairs), qq_out
+// unused.  Same tiling and thread roles as bt_row_pass.
+__device__ __forceinline__ void bt_cascade(f2& acc, float a, f2 x) {
+    float p, pe;
+    two_prod(a, x.hi, p, pe);
+    pe = fmaf(a, x.lo, pe);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo += e + pe;
+}
+template <int KC>
+__device__ void bt_residual_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int k, float* As,
+                                 const f2* Xs, f2* Qs, f2* Wp) {
+    constexpr int CQ = KC < 4 ? KC : 4;
+    constexpr int CG = KC / CQ;
+    constexpr int JS = 8 / CG;
+    const int tid = threadIdx.x;
+    const int n = (int)P.n, npad = (int)P.npad, nch = npad / 4;
+    const int64_t rows = r_hi > r_lo ? r_hi - r_lo : 0;
+    const int ntile = (int)((rows + BR - 1) / BR);
+    const int units = nch * CG;
+    const int RS = units >= BT ? 1 : BT / units;
+    const bool wact = tid < units * RS;
+    const int unit = tid % units, rs = tid / units;
+    const int jg = unit / CG, cgw = unit % CG;
+    f2 acc[4][CQ];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < CQ; ++c) acc[u][c] = f2{0.f, 0.f};
+    const int qr = tid >> 3, qsub = tid & 7, qcg = qsub % CG, qjs = qsub / CG;
+    auto load_tile = [&](int t, int buf) {
+        float* dst = As + buf * BR * LDS;
+        const int64_t row0 = r_lo + (int64_t)t * BR;
+        for (int q = tid; q < BR * nch; q += BT) {
+            const int r = q / nch, ch = q % nch;
+            const int64_t i = row0 + r;
+            const bool ok = i < r_hi;
+            cp_async16(dst + r * LDS + 4 * ch, P.A + (ok ? i : r_lo) * P.ld + 4 * ch, ok);
+        }
+        cp_async_commit();
+    };
+    if (ntile > 0) load_tile(0, 0);
+    for (int t = 0; t < ntile; ++t) {
+        cp_async_wait_all();
+        __syncthreads();
+        if (t + 1 < ntile) load_tile(t + 1, (t + 1) & 1);
+        float* At = As + (t & 1) * BR * LDS;
+        if (n < npad) {
+            const int pw = npad - n;
+            for (int q = tid; q < BR * pw; q += BT) At[(q / pw) * LDS + n + q % pw] = 0.f;
+            __syncthreads();
+        }
+        {   // Q = b - A x for this tile's rows
+            f2 sacc[CQ];
+#pragma unroll
+            for (int c = 0; c < CQ; ++c) sacc[c] = f2{0.f, 0.f};
+            for (int ch = qjs; ch < nch; ch += JS) {
+                const float4 a4 = *reinterpret_cast<const float4*>(At + qr * LDS + 4 * ch);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const f2* xr = Xs + (4 * ch + u) * KC + qcg * CQ;
+#pragma unroll
+                    for (int c = 0; c < CQ; ++c) bt_cascade(sacc[c], av[u], xr[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CQ; ++c) sacc[c] = df_norm(sacc[c]);
+#pragma unroll
+            for (int o = CG; o < 8; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < CQ; ++c) df_add(sacc[c], df_shfl_xor(sacc[c], o));
+            if (qjs == 0) {
+                const int64_t i = r_lo + (int64_t)t * BR + qr;
+                const bool ok = i < r_hi;
+#pragma unroll
+                for (int cc = 0; cc < CQ; ++cc) {
+                    const int c = qcg * CQ + cc;
+                    f2 q = f2{0.f, 0.f};
+                    if (ok && c < k) q = df_from_double(P.B[(int64_t)c * P.ldb + i] - df_to_double(sacc[cc]));
+                    Qs[qr * KC + c] = q;
+                }
+            }
+        }
+        __syncthreads();
+        if (wact) {   // W += A^T Q
+            for (int r = rs; r < BR; r += RS) {
+                const float4 a4 = *reinterpret_cast<const float4*>(At + r * LDS + 4 * jg);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+                f2 qv[CQ];
+#pragma unroll
+                for (int c = 0; c < CQ; ++c) qv[c] = Qs[r * KC + cgw * CQ + c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int c = 0; c < CQ; ++c) bt_cascade(acc[u][c], av[u], qv[c]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int gph = 0; gph < RS; ++gph) {
+        if (wact && rs == gph) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int c = 0; c < CQ; ++c) {
+                    const int at = (4 * jg + u) * KC + cgw * CQ + c;
+                    f2 v = df_norm(acc[u][c]);
+                    if (gph > 0) df_add(v, Wp[at]);
+                    Wp[at] = v;
+                }
+        }
+        __syncthreads();
+    }
+}
+
 // Per-column state of the problem being solved, identical in every CTA of the cluster
 // (each CTA computes it from the same cluster sums in the same order)
 struct BtState {
@@ -251,11 +373,11 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
     using Ly = BLayout<KC>;
     float* As = reinterpret_cast<float*>(smem + Ly::as);
     float* Xf = reinterpret_cast<float*>(smem + Ly::xs);
-    double* Xd = reinterpret_cast<double*>(smem + Ly::xs);
+    f2* Xp = reinterpret_cast<f2*>(smem + Ly::xs);
     float* Wf = reinterpret_cast<float*>(smem + Ly::wp);
-    double* Wd = reinterpret_cast<double*>(smem + Ly::wp);
+    f2* Wpp = reinterpret_cast<f2*>(smem + Ly::wp);
     float* Qf = reinterpret_cast<float*>(smem + Ly::qs);
-    double* Qd = reinterpret_cast<double*>(smem + Ly::qs);
+    f2* Qp = reinterpret_cast<f2*>(smem + Ly::qs);
     double* red = reinterpret_cast<double*>(smem + Ly::red);
     BtState* S = reinterpret_cast<BtState*>(smem + Ly::st);
     const int tid = threadIdx.x;
@@ -276,16 +398,16 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
     auto residual = [&](bool from_zero, double* dst) {
         for (int e = tid; e < NK; e += BT) {
             const int j = e / KC;
-            Xd[e] = (!from_zero && j < n) ? __ldcg(y + e) * P.inv_d[j] : 0.0;
+            Xp[e] = df_from_double((!from_zero && j < n) ? __ldcg(y + e) * P.inv_d[j] : 0.0);
         }
         __syncthreads();
-        bt_row_pass<KC, double>(P, r_lo, r_hi, 1, k, As, Xd, Qd, Wd, S->qq, red);
+        bt_residual_pass<KC>(P, r_lo, r_hi, k, As, Xp, Qp, Wpp);
         cl.sync();
         double a = 0.0, b = 0.0;
         for (int e = e_lo + tid; e < e_hi; e += BT) {
             const int j = e / KC;
             double sum = 0.0;
-            for (int r = 0; r < C; ++r) sum += cl.map_shared_rank(Wd, r)[e];
+            for (int r = 0; r < C; ++r) sum += df_to_double(cl.map_shared_rank(Wpp, r)[e]);
             const double v = j < n ? sum * P.inv_d[j] : 0.0;
             dst[e] = v;
             a = fma(v, v, a);

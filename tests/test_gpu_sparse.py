@@ -10,6 +10,18 @@ from helpers import rel, to_device
 pytestmark = pytest.mark.gpu
 
 
+def _same_solution(seen, d, x_gpu, y_or, b, tol):
+    """Both solutions meet the normal equation to tol, so Â^T Â (y_gpu - y_or) is the
+    difference of their two residuals: its norm is at most (tol_gpu + tol_or) ||Â^T b||.
+    This checks the GPU solution against the oracle's without forming or factoring Â."""
+    import scipy.sparse as sps
+    A = sps.csr_matrix((seen["vals"], seen["col_idx"], seen["row_ptr"]), shape=(seen["m"], seen["n"]))
+    Ah = A @ sps.diags(1.0 / d)
+    dy = x_gpu * d - y_or
+    h = Ah.T @ b
+    return np.linalg.norm(Ah.T @ (Ah @ dy)) <= 2.05 * tol * np.linalg.norm(h)
+
+
 def _setup(lsq, orc, mat, seed, sweeps=1, dtype="f64", pdt=0, with_f64=False):
     Mx, keep, seen = to_device(lsq, mat, dtype, with_f64=with_f64)
     o = lsq.opts(seed=seed, sweeps=sweeps, precond_dtype=pdt)
@@ -56,14 +68,17 @@ def test_sparse_pcg_matches_oracle(lsq, orc, case, noise):
     xs, b = W.rhs_for(seen, 2, noise, 17)
     X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
     X = X.cpu().numpy()
-    A = W.dense_from_csr(seen)
-    kappa = np.linalg.cond(A / smp.d)
+    small = seen["n"] <= 5000
+    if small:
+        kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
     for c in range(2):
         y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
         x_or = y / smp.d
         assert info.converged[c] == 1 and oi["converged"] == 1
         assert info.relres_true[c] <= o.tol
-        assert rel(X[c], x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        if small:
+            assert rel(X[c], x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert _same_solution(seen, smp.d, X[c], y, b[c], o.tol)
         assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info.iters[c], oi["iters"])
     assert info.nnz_M == Mo.val.size
     # forward level count of Alg. 3's dependency DAG, computed here from M's pattern
@@ -109,11 +124,13 @@ def test_sparse_pcg_single_column_matches_oracle(lsq, orc, case):
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 2029)
     xs, b = W.rhs_for(seen, 1, 1e-3, 23)
     X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
-    A = W.dense_from_csr(seen)
-    kappa = np.linalg.cond(A / smp.d)
     y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
     assert info.converged[0] == 1 and oi["converged"] == 1
-    assert rel(X.cpu().numpy().reshape(-1), y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+    x = X.cpu().numpy().reshape(-1)
+    if seen["n"] <= 5000:
+        kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
+        assert rel(x, y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+    assert _same_solution(seen, smp.d, x, y, b[0], o.tol)
     assert abs(int(info.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
 
 

@@ -43,7 +43,9 @@ def _check_against_oracle(orc, pr, X, info, tol, cols):
         assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * tol)
         r = A.T @ (pr["b"][c] - A @ X[c])
         raw = np.linalg.norm(r) / np.linalg.norm(A.T @ pr["b"][c])
-        assert abs(raw - info.relres_raw[c]) <= 1e-3 * raw + 1e-15
+        # the batch computes its residuals in double-float (~48 bits): near roundoff the
+        # reported ratio carries an absolute error of a few 1e-15
+        assert abs(raw - info.relres_raw[c]) <= 1e-3 * raw + 1e-13
 
 
 def test_batch_uneven_matches_oracle(lsq, orc):

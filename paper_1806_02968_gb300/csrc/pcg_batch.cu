@@ -33,18 +33,22 @@ namespace cg = cooperative_groups;
 
 namespace lsq {
 
-constexpr int BT = 256;            // threads per CTA
+constexpr int BT = 512;            // threads per CTA (16 warps; 128 registers each)
 constexpr int BR = 32;             // rows per tile
+constexpr int TPR = BT / BR;       // threads per tile row in the Q step (16)
 constexpr int NPMAX = 256;         // largest padded n
 constexpr int LDS = NPMAX + 8;     // shared-memory pitch of a tile row (floats; 8 keeps
                                    // the float4 reads of 4 rows on distinct banks)
 
 // Shared-memory layout for KC columns (byte offsets; every part 16-byte aligned)
+// P~ / x rows in shared memory are XP entries apart: 4 entries of padding (from 4 columns up)
+// put the rows that the threads of one tile row read together on different banks
+template <int KC> struct XPitch { static constexpr int v = KC >= 4 ? KC + 4 : KC; };
 template <int KC>
 struct BLayout {
     static constexpr size_t as = 0;                                   // two A tiles (float)
-    static constexpr size_t xs = as + 2 * (size_t)BR * LDS * 4;       // P~ (float) or x (double)
-    static constexpr size_t wp = xs + (size_t)NPMAX * KC * 8;         // this CTA's W
+    static constexpr size_t xs = as + 2 * (size_t)BR * LDS * 4;       // P~ (float) or x (pairs)
+    static constexpr size_t wp = xs + (size_t)NPMAX * XPitch<KC>::v * 8;   // this CTA's W
     static constexpr size_t qs = wp + (size_t)NPMAX * KC * 8;         // Q of the current tile
     static constexpr size_t red = qs + (size_t)BR * KC * 8;           // reduction scratch
     static constexpr size_t st = red + (size_t)BT * 4 * 8;            // per-column state
@@ -66,7 +70,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //   Wp = A^T Q over these rows, qq_out[c] = sum of Q_ic^2 over these rows (c < k)
 // X (npad x KC, rows j >= n zero) is in shared memory.  Tiles of BR rows are streamed with
 // cp.async into two buffers; the next tile is in flight while the current one is used.
-// Q step: 8 threads per tile row, each CQ columns over a JS-th of the row, combined by
+// Q step: TPR threads per tile row, each CQ columns over a JS-th of the row, combined by
 // shuffles.  W step: a thread owns 4 consecutive j and CQ columns (RS threads split the rows
 // when there are fewer such units than threads) and accumulates over all tiles in registers.
 template <int KC, typename T>
@@ -74,7 +78,7 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
                             float* As, const T* Xs, T* Qs, T* Wp, double* qq_out, double* red) {
     constexpr int CQ = KC < 4 ? KC : 4;
     constexpr int CG = KC / CQ;
-    constexpr int JS = 8 / CG;
+    constexpr int JS = TPR / CG;
     const int tid = threadIdx.x;
     const int n = (int)P.n, npad = (int)P.npad, nch = npad / 4;
     const int64_t rows = r_hi > r_lo ? r_hi - r_lo : 0;
@@ -92,7 +96,7 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
     double qq[CQ];
 #pragma unroll
     for (int c = 0; c < CQ; ++c) qq[c] = 0.0;
-    const int qr = tid >> 3, qsub = tid & 7, qcg = qsub % CG, qjs = qsub / CG;
+    const int qr = tid / TPR, qsub = tid % TPR, qcg = qsub % CG, qjs = qsub / CG;
 
     auto load_tile = [&](int t, int buf) {
         float* dst = As + buf * BR * LDS;
@@ -125,13 +129,21 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
                 const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const T* xr = Xs + (4 * ch + u) * KC + qcg * CQ;
+                    const T* xr = Xs + (4 * ch + u) * XPitch<KC>::v + qcg * CQ;
+                    T xv[CQ];
+                    if constexpr (CQ == 4 && sizeof(T) == 4) {
+                        const float4 x4 = *reinterpret_cast<const float4*>(xr);
+                        xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < CQ; ++c) sacc[c] = fma((T)av[u], xr[c], sacc[c]);
+                        for (int c = 0; c < CQ; ++c) xv[c] = xr[c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < CQ; ++c) sacc[c] = fma((T)av[u], xv[c], sacc[c]);
                 }
             }
 #pragma unroll
-            for (int o = CG; o < 8; o <<= 1)
+            for (int o = CG; o < TPR; o <<= 1)
 #pragma unroll
                 for (int c = 0; c < CQ; ++c) sacc[c] += __shfl_xor_sync(0xffffffffu, sacc[c], o);
             if (qjs == 0) {
@@ -186,7 +198,7 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
     if (tid < KC) {
         const int g = tid / CQ, cc = tid % CQ;
         double sum = 0.0;
-        for (int r = 0; r < BR; ++r) sum += red[(r * 8 + g) * CQ + cc];
+        for (int r = 0; r < BR; ++r) sum += red[(r * TPR + g) * CQ + cc];
         qq_out[tid] = sum;
     }
     __syncthreads();
@@ -210,7 +222,7 @@ __device__ void bt_residual_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi,
                                  const f2* Xs, f2* Qs, f2* Wp) {
     constexpr int CQ = KC < 4 ? KC : 4;
     constexpr int CG = KC / CQ;
-    constexpr int JS = 8 / CG;
+    constexpr int JS = TPR / CG;
     const int tid = threadIdx.x;
     const int n = (int)P.n, npad = (int)P.npad, nch = npad / 4;
     const int64_t rows = r_hi > r_lo ? r_hi - r_lo : 0;
@@ -225,7 +237,7 @@ __device__ void bt_residual_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi,
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int c = 0; c < CQ; ++c) acc[u][c] = f2{0.f, 0.f};
-    const int qr = tid >> 3, qsub = tid & 7, qcg = qsub % CG, qjs = qsub / CG;
+    const int qr = tid / TPR, qsub = tid % TPR, qcg = qsub % CG, qjs = qsub / CG;
     auto load_tile = [&](int t, int buf) {
         float* dst = As + buf * BR * LDS;
         const int64_t row0 = r_lo + (int64_t)t * BR;
@@ -257,7 +269,7 @@ __device__ void bt_residual_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi,
                 const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const f2* xr = Xs + (4 * ch + u) * KC + qcg * CQ;
+                    const f2* xr = Xs + (4 * ch + u) * XPitch<KC>::v + qcg * CQ;
 #pragma unroll
                     for (int c = 0; c < CQ; ++c) bt_cascade(sacc[c], av[u], xr[c]);
                 }
@@ -265,7 +277,7 @@ __device__ void bt_residual_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi,
 #pragma unroll
             for (int c = 0; c < CQ; ++c) sacc[c] = df_norm(sacc[c]);
 #pragma unroll
-            for (int o = CG; o < 8; o <<= 1)
+            for (int o = CG; o < TPR; o <<= 1)
 #pragma unroll
                 for (int c = 0; c < CQ; ++c) df_add(sacc[c], df_shfl_xor(sacc[c], o));
             if (qjs == 0) {
@@ -386,6 +398,7 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
     const int64_t r_lo = P.m * rank / C, r_hi = P.m * (rank + 1) / C;
     const int e_lo = (int)((int64_t)npad * rank / C) * KC, e_hi = (int)((int64_t)npad * (rank + 1) / C) * KC;
     const int NK = npad * KC;
+    constexpr int XP = XPitch<KC>::v;
     double* y = P.ws;
     double* g = y + NK;
     double* z = g + NK;
@@ -397,8 +410,8 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
     // S->t0 = ||dst||^2, S->t1 = ||A^T (b - A x)||^2 per column
     auto residual = [&](bool from_zero, double* dst) {
         for (int e = tid; e < NK; e += BT) {
-            const int j = e / KC;
-            Xp[e] = df_from_double((!from_zero && j < n) ? __ldcg(y + e) * P.inv_d[j] : 0.0);
+            const int j = e / KC, c = e % KC;
+            Xp[j * XP + c] = df_from_double((!from_zero && j < n) ? __ldcg(y + e) * P.inv_d[j] : 0.0);
         }
         __syncthreads();
         bt_residual_pass<KC>(P, r_lo, r_hi, k, As, Xp, Qp, Wpp);
@@ -421,7 +434,7 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
     };
     // z = (SGS operator) g on this CTA's slice, FP32 arithmetic; S->t0 = g^T z per column
     auto apply_op = [&]() {
-        for (int e = tid; e < NK; e += BT) Xf[e] = (float)__ldcg(g + e);
+        for (int e = tid; e < NK; e += BT) Xf[(e / KC) * XP + e % KC] = (float)__ldcg(g + e);
         __syncthreads();
         double a = 0.0;
         for (int e = e_lo + tid; e < e_hi; e += BT) {
@@ -431,10 +444,10 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
                 float sacc = 0.f;
                 if (P.op_f32) {
                     const float* o = reinterpret_cast<const float*>(P.op) + (int64_t)j * n;
-                    for (int l = 0; l < n; ++l) sacc = fmaf(o[l], Xf[l * KC + c], sacc);
+                    for (int l = 0; l < n; ++l) sacc = fmaf(o[l], Xf[l * XP + c], sacc);
                 } else {
                     const double* o = reinterpret_cast<const double*>(P.op) + (int64_t)j * n;
-                    for (int l = 0; l < n; ++l) sacc = fmaf((float)o[l], Xf[l * KC + c], sacc);
+                    for (int l = 0; l < n; ++l) sacc = fmaf((float)o[l], Xf[l * XP + c], sacc);
                 }
                 zv = sacc;
             }
@@ -457,7 +470,7 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
                 p[e] = pv;
                 if (j < n) pt = (float)(pv * P.inv_d[j]);
             }
-            for (int r = 0; r < C; ++r) cl.map_shared_rank(Xf, r)[e] = pt;
+            for (int r = 0; r < C; ++r) cl.map_shared_rank(Xf, r)[j * XP + c] = pt;
         }
         cl.sync();
     };

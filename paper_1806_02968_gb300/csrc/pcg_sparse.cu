@@ -525,11 +525,14 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
     return LSQ_OK;
 }
 
-// One CTA per sweep when levels hold fewer than 256 rows on average: block barriers between
-// levels are then cheaper than a grid of warps waiting on completion counters.
+// One CTA per sweep when a level holds fewer than 2048 dependency entries on average: block
+// barriers between levels are then cheaper than a grid of warps waiting on completion
+// counters, and one SM's loads still keep up with a level's gathers (at ~10,000 entries per
+// level one SM is twice slower than the grid).
 static void choose_sweep_form(SpArgs& a, const SparseHandle* SH, int64_t n) {
-    a.one_f = SH->nlev_f * 256 > n ? SH->nlev_f : 0;
-    a.one_b = SH->nlev_b * 256 > n ? SH->nlev_b : 0;
+    const double dep = 0.5 * (double)(SH->nnz_M - n);   // dependency entries per direction
+    a.one_f = dep < 2048.0 * (double)SH->nlev_f ? SH->nlev_f : 0;
+    a.one_b = dep < 2048.0 * (double)SH->nlev_b ? SH->nlev_b : 0;
 }
 
 static unsigned gridn(int64_t work, int64_t cap = 152 * 8) {

@@ -421,21 +421,35 @@ __global__ void __launch_bounds__(256) k_levels(int64_t n, const int64_t* mptr, 
         const int64_t j = FWD ? t : n - 1 - t;
         const int64_t d0 = FWD ? mptr[j] : mdiag[j] + 1, d1 = FWD ? mdiag[j] : mptr[j + 1];
         int mx = 0;
-        for (int64_t e = d0 + lane; e < d1; e += 32) {
-            const int32_t k = mcol[e];
-            int v = ld_acquire_i32(lev1 + k);
+        // the dependencies in batches of 8 per lane: all loads of a batch are issued
+        // together, then only the ones not known yet are polled again
+        for (int64_t base = d0 + lane; base < d1; base += 32 * 8) {
+            int32_t kk[8];
+            int v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) kk[u] = base + 32 * u < d1 ? mcol[base + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = kk[u] >= 0 ? ld_acquire_i32(lev1 + kk[u]) : 1;
             unsigned polls = 0, ns = 32;
-            while (v == 0) {
+            while (true) {
+                bool missing = false;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) missing = missing || v[u] == 0;
+                if (!missing) break;
                 ++polls;
                 if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
                     atomicOr(err, DEV_ERR_TIMEOUT);
-                    v = 1;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = max(v[u], 1);
                     break;
                 }
-                if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
-                v = ld_acquire_i32(lev1 + k);
+                if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (v[u] == 0) v[u] = ld_acquire_i32(lev1 + kk[u]);
             }
-            mx = max(mx, v);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = max(mx, v[u]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));

@@ -5,12 +5,14 @@
 //   k_sp_rows   q = Â p over the rows of A (CSR), partials of ||q||^2 = p^T w
 //   k_sp_cols   w = Â^T q over the columns (the cached transposed pattern; no atomics)
 //   k_sp_update alpha = rho / p^T w, y += alpha p, g -= alpha w, partials of ||g||^2
-//   k_sp_sweep  forward then backward Gauss-Seidel sweep (the first checks convergence)
+//   sweeps      forward then backward Gauss-Seidel sweeps (the first checks convergence):
+//               k_sp_sweep_vf on the grid, or k_sp_sweep_1cta in one CTA for narrow levels
 //   k_sp_pnext  rho' = g^T z, beta, p = z + beta p
 // The sweeps keep the natural row order of Alg. 3: a row depends on the rows of its lower
-// (forward) or upper (backward) entries.  Rows run in level order, each waiting on a
-// per-level completion count (bounded waits; see k_sp_sweep).  A device flag ends the
-// remaining kernels of a batch once PCG has converged.
+// (forward) or upper (backward) entries.  Rows run in level order; on the grid each row
+// waits (bounded) for the values of its own dependencies, in one CTA the levels meet at
+// block barriers.  A device flag ends the remaining kernels of a batch once PCG has
+// converged.
 #include "sparse.cuh"
 #include "values.cuh"
 
@@ -176,21 +178,28 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 //   e_new_j = (r_j - sum_{other side} M_jk e_old_k - sum_{dependency side} M_jk e_new_k) / M_jj
 // With `identity` (the backward sweep right after a single forward sweep from zero,
 // t = 1): r - L e_old = D e_old, so e_new_j = e_old_j - (sum_{k>j} M_jk e_new_k) / M_jj.
-//
-// Level scheduling without grid barriers.  The launch is cooperative (every warp resident);
-// warp w takes schedule slots w, w + W, w + 2W, ... (rows sorted by level), so it meets its
-// rows in level order.  A row of level L loads its entries and adds its other-side terms,
-// then waits until every row of level L-1 has finished this sweep: 32 cumulative
-// sub-counters per level on separate cache lines (rows add to sub-counter w mod 32, a
-// waiting warp sums all 32, one per lane), acquire/release ordering, bounded polls with
-// exponential backoff.  Rows of level L depend only on lower
-// levels, which every warp finishes first, so the wait always ends.
-// `check` (first sweep of an iteration): reduce ||g||^2 first and stop when converged.
-constexpr int SW_PF = 16;           // entries per lane held in registers before the wait
+constexpr int SW_PF = 16;           // dependency entries per lane held in registers
+
+// The grid sweep with the values themselves as completion flags.  Before the sweep every slot
+// of e_new holds SWEEP_EMPTY, a signalling NaN that no arithmetic produces; a row polls the
+// values it depends on (volatile loads, bounded) until none is SWEEP_EMPTY, then writes its own
+// value.  A row thus waits for its own dependencies only, and no counter has to be published
+// and read back between levels.  Warp w takes schedule slots w, w + W, ... (rows sorted by
+// level), all warps resident, so every wait ends.
+constexpr unsigned long long SWEEP_EMPTY = 0xFFF7DEADBEEFCAFEull;
+__global__ void k_fill_empty(double* e, int64_t n) {
+    unsigned long long* u = reinterpret_cast<unsigned long long*>(e);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        u[j] = SWEEP_EMPTY;
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const double* p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 template <typename MT, bool FWD>
-__global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, const double* e_old,
-                                                   double* e_new, int identity, int check, int nparts,
-                                                   int sweep_idx) {
+__global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r, const double* e_old,
+                                                      double* e_new, int identity, int check, int nparts) {
     __shared__ double sh[40];
     __shared__ int s_stop;
     if (a.S->done) return;
@@ -210,11 +219,6 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
             return;
         }
     }
-    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;   // sweep number within its direction
-    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
-    unsigned long long* done = FWD ? a.done_f : a.done_b;
-    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
-    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
     const int32_t* sched = FWD ? a.sched_f : a.sched_b;
     const MT* mv = reinterpret_cast<const MT*>(a.mval);
     const int lane = threadIdx.x & 31;
@@ -222,81 +226,64 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep(SpArgs a, const double* r, co
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool other = !identity && e_old != nullptr;
     bool ok = true;
+    // the values of up to 8 dependencies per lane: issue all loads, then poll the missing
+    auto gather8 = [&](const int32_t (&kk)[8], const double (&mm)[8], double& acc) {
+        unsigned long long u[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) u[c] = kk[c] >= 0 ? ld_volatile_u64(e_new + kk[c]) : 0ull;
+        unsigned polls = 0, ns = 32;
+        while (true) {
+            bool missing = false;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) missing = missing || (kk[c] >= 0 && u[c] == SWEEP_EMPTY);
+            if (!missing) break;
+            ++polls;
+            if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+                ok = false;
+                atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) if (u[c] == SWEEP_EMPTY) u[c] = 0ull;
+                break;
+            }
+            if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (kk[c] >= 0 && u[c] == SWEEP_EMPTY) u[c] = ld_volatile_u64(e_new + kk[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (kk[c] >= 0) acc = fma(mm[c], __longlong_as_double((long long)u[c]), acc);
+    };
     for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
-        const int L = lvl[slot];
-        // rows are sorted and hold their diagonal: the dependency side (lower entries forward,
-        // upper backward) and the other side are the two ranges around it
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
         const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
         double acc = 0.0;
-        if (other)   // the previous sweep's values: no wait needed
+        if (other)
             for (int64_t e = o0 + lane; e < o1; e += 32) acc = fma((double)mv[e], e_old[a.mcol[e]], acc);
-        // the first 32*SW_PF dependency entries, in registers before the wait
-        int32_t kk[SW_PF];
-        double mm[SW_PF];
+        const double base = identity ? e_old[j] : r[j];
+        const double dj = a.dinv[j];
+        for (int64_t b0 = d0 + lane; b0 < d1; b0 += 32 * 8) {
+            int32_t kk[8];
+            double mm[8];
 #pragma unroll
-        for (int c = 0; c < SW_PF; ++c) {
-            const int64_t e = d0 + lane + 32 * c;
-            kk[c] = -1;
-            mm[c] = 0.0;
-            if (e < d1) { kk[c] = a.mcol[e]; mm[c] = (double)mv[e]; }
-        }
-        if (L > 0) {
-            const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
-            const unsigned long long* cnt = done + (int64_t)(L - 1) * LVL_WORDS;
-            unsigned polls = 0, ns = 32;
-            while (true) {
-                unsigned long long v = ld_acquire_u64(&cnt[lane * LVL_STRIDE]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (v >= target) break;
-                // one failed wait ends them all: it sets the error word, which every wait
-                // checks while polling
-                ++polls;
-                const bool give_up = polls > (1u << 22) ||
-                                     ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u);
-                if (__any_sync(0xffffffffu, give_up)) {
-                    ok = false;
-                    if (lane == 0) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
-                    break;
-                }
-                if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+            for (int c = 0; c < 8; ++c) {
+                const int64_t e = b0 + 32 * c;
+                kk[c] = -1;
+                mm[c] = 0.0;
+                if (e < d1) { kk[c] = a.mcol[e]; mm[c] = (double)mv[e]; }
             }
-            // each lane acquired one sub-counter; the warp barrier orders every lane's loads
-            // below after all 32 acquires
-            __syncwarp();
-        }
-#pragma unroll
-        for (int c = 0; c < SW_PF; ++c)
-            if (kk[c] >= 0) acc = fma(mm[c], e_new[kk[c]], acc);
-        // long rows: the rest of the dependency side, indices of 8 chunks first, then gathers
-        for (int64_t base = d0 + 32 * SW_PF; base < d1; base += 32 * 8) {
-            int32_t k2[8];
-            double m2[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t e = base + lane + 32 * u;
-                k2[u] = -1;
-                m2[u] = 0.0;
-                if (e < d1) { k2[u] = a.mcol[e]; m2[u] = (double)mv[e]; }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (k2[u] >= 0) acc = fma(m2[u], e_new[k2[u]], acc);
+            gather8(kk, mm, acc);
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-            const double dj = a.dinv[j];
-            const double v = identity ? e_old[j] - acc * dj : (r[j] - acc) * dj;
-            e_new[j] = v;
-            red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (gw & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
+            const double v = identity ? base - acc * dj : (base - acc) * dj;
+            asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(e_new + j), "d"(v) : "memory");
         }
         __syncwarp();
     }
-    const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
-    if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+    (void)ok;
 }
 
 // The same sweep in ONE CTA, for deep and narrow level structures (few rows per level): the
@@ -502,7 +489,7 @@ template <typename MT, bool FWD>
 static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* eold, double* enew,
                                int identity, int check, int nparts, int idx, cudaStream_t st) {
     static int grid = 0;
-    auto kern = k_sp_sweep<MT, FWD>;
+    auto kern = k_sp_sweep_vf<MT, FWD>;
     if (grid == 0) {
         int dev = 0, sms = 0, per = 0;
         LSQ_CUDA(cudaGetDevice(&dev));
@@ -518,8 +505,12 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
         LSQ_CUDA(cudaGetLastError());
         return LSQ_OK;
     }
+    // the grid form: fill e_new with the empty marker, then the value-flag sweep
+    k_fill_empty<<<(unsigned)std::min<int64_t>((a.n + SP_T - 1) / SP_T, 152 * 8), SP_T, 0, st>>>(enew, a.n);
+    count_launch();
+    (void)idx;
     SpArgs av = a;
-    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &check, &nparts, &idx};
+    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &check, &nparts};
     LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(SP_T), params, 0, st));
     count_launch();
     return LSQ_OK;

@@ -93,9 +93,10 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int c = 0; c < CQ; ++c) acc[u][c] = T(0);
-    double qq[CQ];
+    // ||Q||^2 in double-float on the FP32 units (the FP64 pipe runs at 1/64 of their rate)
+    f2 qq[CQ];
 #pragma unroll
-    for (int c = 0; c < CQ; ++c) qq[c] = 0.0;
+    for (int c = 0; c < CQ; ++c) qq[c] = f2{0.f, 0.f};
     const int qr = tid / TPR, qsub = tid % TPR, qcg = qsub % CG, qjs = qsub / CG;
 
     auto load_tile = [&](int t, int buf) {
@@ -156,7 +157,7 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
                     if (ok && c < k) {
                         q = sacc[cc];
                         if (mode == 1) q = (T)(P.B[(int64_t)c * P.ldb + i] - (double)sacc[cc]);
-                        qq[cc] = fma((double)q, (double)q, qq[cc]);
+                        df_add_sq(qq[cc], (float)q);
                     }
                     Qs[qr * KC + c] = q;
                 }
@@ -193,7 +194,7 @@ __device__ void bt_row_pass(const BatchProb& P, int64_t r_lo, int64_t r_hi, int 
     }
     // ||Q||^2 per column: the js == 0 threads of every tile row, in row order
 #pragma unroll
-    for (int c = 0; c < CQ; ++c) red[tid * CQ + c] = (qjs == 0) ? qq[c] : 0.0;
+    for (int c = 0; c < CQ; ++c) red[tid * CQ + c] = (qjs == 0) ? df_to_double(qq[c]) : 0.0;
     __syncthreads();
     if (tid < KC) {
         const int g = tid / CQ, cc = tid % CQ;

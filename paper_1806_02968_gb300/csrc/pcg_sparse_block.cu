@@ -69,8 +69,6 @@ struct BkArgs {
     const int32_t* lvl_b;
     const int64_t* lsize_f;
     const int64_t* lsize_b;
-    unsigned long long* done_f;
-    unsigned long long* done_b;
     int sweeps;
     double *y, *g, *z, *p, *pt, *w, *q, *e0, *e1, *h;
     double* part;             // per-block partials, [blocks][K] (x2 for the norms)
@@ -282,52 +280,67 @@ __global__ void __launch_bounds__(BK_T) k_bk_update(BkArgs a) {
     if (threadIdx.x == 0 && !s_any) a.S->done = 1;
 }
 
-// Wait until every row of level L-1 has finished the current sweep: the 32 completion
-// sub-counters of that level (separate cache lines), one per lane, summed by the warp
-// (acquire loads, bounded polls with exponential backoff).
-// A wait that gives up sets DEV_ERR_TIMEOUT in *err at once, and every wait checks *err while
-// polling, so one failure ends all waits of the launch instead of each running to its bound.
-__device__ __forceinline__ bool bk_level_wait(const unsigned long long* done, int L, unsigned long long epoch,
-                                              const int64_t* lsz, int lane, unsigned* err) {
-    if (L == 0) return true;
-    const unsigned long long target = epoch * (unsigned long long)lsz[L - 1];
-    const unsigned long long* cntp = done + (int64_t)(L - 1) * LVL_WORDS;
+// Gauss-Seidel sweeps of Alg. 3 for all K columns, with the values themselves as completion
+// flags: before a sweep every entry of e_new holds BK_EMPTY, a signalling NaN that no
+// arithmetic produces; a row polls the values it depends on (volatile loads, issued in
+// batches, bounded) until none is BK_EMPTY, then stores its own.  Rows run in level order over
+// a cooperative grid, so every wait ends; a row waits for its real dependencies only.  One
+// failed wait sets the error word, which every wait checks, so a failure ends the launch within
+// one wait bound.  Rows are sorted and hold their diagonal: the dependency side (lower entries
+// forward, upper backward) and the other side are the two ranges around it.  `identity`: the
+// backward sweep right after one forward sweep from zero (e_new = e_old - upper terms / M_jj).
+constexpr unsigned long long BK_EMPTY = 0xFFF7DEADBEEFCAFEull;
+__global__ void k_bk_fill_empty(double* e, int64_t cnt) {
+    unsigned long long* u = reinterpret_cast<unsigned long long*>(e);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        u[t] = BK_EMPTY;
+}
+__device__ __forceinline__ unsigned long long bk_ldv(const double* p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void bk_stv(double* p, double v) {
+    asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+// Loads N values (use[i] false: skipped), polling the missing ones until all are written.
+template <int N>
+__device__ __forceinline__ bool bk_gather_ready(const double* const* ptr, const bool* use, double* out,
+                                                unsigned* err) {
+    unsigned long long u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = use[i] ? bk_ldv(ptr[i]) : 0ull;
     unsigned polls = 0, ns = 32;
     bool ok = true;
     while (true) {
-        unsigned long long v = bk_ld_acquire_u64(&cntp[lane * LVL_STRIDE]);
+        bool missing = false;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (v >= target) break;
+        for (int i = 0; i < N; ++i) missing = missing || (use[i] && u[i] == BK_EMPTY);
+        if (!missing) break;
         ++polls;
-        const bool give_up = polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u);
-        if (__any_sync(0xffffffffu, give_up)) {
+        if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
             ok = false;
-            if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+#pragma unroll
+            for (int i = 0; i < N; ++i) if (u[i] == BK_EMPTY) u[i] = 0ull;
             break;
         }
-        if (polls > 8) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+        if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (use[i] && u[i] == BK_EMPTY) u[i] = bk_ldv(ptr[i]);
     }
-    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = use[i] ? __longlong_as_double((long long)u[i]) : 0.0;
     return ok;
 }
 
-// One Gauss-Seidel sweep of Alg. 3 for all K columns, level-ordered without grid barriers
-// (cooperative launch; warp w takes schedule slots w, w + W, ... in level order; a row of
-// level L waits for level L-1).  Rows are sorted and hold their diagonal, so the dependency
-// side (lower entries forward, upper backward) and the other side are the two ranges around
-// it.  This form is for short rows: a warp takes a row, its entries are loaded 32 at a time
-// and broadcast by shuffles, and lane c accumulates column c.  `identity`: the backward sweep
-// right after one forward sweep from zero (e_new = e_old - upper terms / M_jj).
+// Short rows: a warp takes a row; its entries are loaded 32 at a time and broadcast by
+// shuffles, 8 gathers in flight per lane; lane c accumulates column c.
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, const double* e_old,
                                                    double* e_new, int identity, int sweep_idx) {
     if (a.S->done) return;
-    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
-    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
-    unsigned long long* done = FWD ? a.done_f : a.done_b;
-    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
-    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
     const int32_t* sched = FWD ? a.sched_f : a.sched_b;
     const MT* mv = reinterpret_cast<const MT*>(a.mval);
     const int lane = threadIdx.x & 31;
@@ -336,15 +349,14 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool other = !identity && e_old != nullptr;
-    bool ok = true;
+    (void)sweep_idx;
     for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
-        const int L = lvl[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
         const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
         double acc = 0.0;
-        if (other) {   // previous sweep's values on the other side: no wait needed
+        if (other) {   // previous sweep's values on the other side: complete already
             for (int64_t base = o0; base < o1; base += 32) {
                 const int64_t e = base + lane;
                 int32_t kk = 0;
@@ -358,50 +370,36 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
                 }
             }
         }
-        int32_t pk[BK_PF];
-        double pm[BK_PF];
-#pragma unroll
-        for (int c = 0; c < BK_PF; ++c) {
-            const int64_t e = d0 + lane + 32 * c;
-            pk[c] = 0;
-            pm[c] = 0.0;
-            if (e < d1) { pk[c] = a.mcol[e]; pm[c] = (double)mv[e]; }
-        }
-        ok = bk_level_wait(done, L, epoch, lsz, lane, &a.S->err) && ok;
-#pragma unroll
-        for (int c = 0; c < BK_PF; ++c) {
-            const int64_t cbase = d0 + 32 * c;
-            if (cbase < d1) {
-                const int cnt = (int)min((int64_t)32, d1 - cbase);
-                for (int t = 0; t < cnt; ++t) {
-                    const int32_t k = __shfl_sync(0xffffffffu, pk[c], t);
-                    const double mk = __shfl_sync(0xffffffffu, pm[c], t);
-                    if (col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
-                }
-            }
-        }
-        for (int64_t base = d0 + 32 * BK_PF; base < d1; base += 32) {   // long rows
+        for (int64_t base = d0; base < d1; base += 32) {
             const int64_t e = base + lane;
             int32_t kk = 0;
             double mm = 0.0;
             if (e < d1) { kk = a.mcol[e]; mm = (double)mv[e]; }
             const int cnt = (int)min((int64_t)32, d1 - base);
-            for (int t = 0; t < cnt; ++t) {
-                const int32_t k = __shfl_sync(0xffffffffu, kk, t);
-                const double mk = __shfl_sync(0xffffffffu, mm, t);
-                if (col_ok) acc = fma(mk, e_new[(int64_t)k * K + lane], acc);
+            for (int t0 = 0; t0 < cnt; t0 += 8) {
+                const double* ptr[8];
+                bool use[8];
+                double mk[8], val[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int t = (t0 + i) & 31;
+                    const int32_t k = __shfl_sync(0xffffffffu, kk, t);
+                    mk[i] = __shfl_sync(0xffffffffu, mm, t);
+                    use[i] = col_ok && t0 + i < cnt;
+                    ptr[i] = e_new + (int64_t)k * K + lane;
+                }
+                bk_gather_ready<8>(ptr, use, val, &a.S->err);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc = fma(mk[i], val[i], acc);
             }
         }
         if (col_ok) {
             const double dj = a.dinv[j];
             const int64_t at = j * K + lane;
-            e_new[at] = identity ? e_old[at] - acc * dj : (r[at] - acc) * dj;
+            bk_stv(e_new + at, identity ? e_old[at] - acc * dj : (r[at] - acc) * dj);
         }
         __syncwarp();
-        if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (gw & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
     }
-    const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
-    if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
 // acc[0..KT) per lane -> lane l holds the warp total of column l >> (5 - log2 KT)
@@ -427,19 +425,46 @@ __device__ __forceinline__ double bk_reduce_scatter(double (&v)[KT], int lane) {
     return v[0];
 }
 
-// The same sweep for long rows: lanes take the row's entries (lane l: entries l, l + 32, ...)
-// and keep KT column accumulators each; one reduce-scatter per row combines them.  The
-// dependency side's first 32*BK_PFE entries are loaded before the level wait.
-constexpr int BK_PFE = 16;
+// One dependency entry for KT column accumulators: its K contiguous values, polled until
+// all are written.
+template <typename MT, int KT>
+__device__ __forceinline__ void bk_entry(const BkArgs& a, const double* e_new, int64_t e, double (&acc)[KT]) {
+    const int K = a.K;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const double* row = e_new + (int64_t)a.mcol[e] * K;
+    const double mk = (double)mv[e];
+    unsigned long long u[KT];
+#pragma unroll
+    for (int c = 0; c < KT; ++c) u[c] = c < K ? bk_ldv(row + c) : 0ull;
+    unsigned polls = 0, ns = 32;
+    while (true) {
+        bool missing = false;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) missing = missing || (c < K && u[c] == BK_EMPTY);
+        if (!missing) break;
+        ++polls;
+        if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+            atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+#pragma unroll
+            for (int c = 0; c < KT; ++c) if (u[c] == BK_EMPTY) u[c] = 0ull;
+            break;
+        }
+        if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+#pragma unroll
+        for (int c = 0; c < KT; ++c)
+            if (c < K && u[c] == BK_EMPTY) u[c] = bk_ldv(row + c);
+    }
+#pragma unroll
+    for (int c = 0; c < KT; ++c)
+        if (c < K) acc[c] = fma(mk, __longlong_as_double((long long)u[c]), acc[c]);
+}
+
+// Long rows: lanes take the row's entries (lane l: entries l, l + 32, ...) and keep KT column
+// accumulators; one reduce-scatter per row combines them.
 template <typename MT, bool FWD, int KT>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r, const double* e_old,
                                                       double* e_new, int identity, int sweep_idx) {
     if (a.S->done) return;
-    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
-    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
-    unsigned long long* done = FWD ? a.done_f : a.done_b;
-    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
-    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
     const int32_t* sched = FWD ? a.sched_f : a.sched_b;
     const MT* mv = reinterpret_cast<const MT*>(a.mval);
     const int lane = threadIdx.x & 31;
@@ -450,10 +475,9 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r,
     constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
     const int my_col = lane >> SH;
     const bool writer = (lane & ((1 << SH) - 1)) == 0 && my_col < K;
-    bool ok = true;
+    (void)sweep_idx;
     for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
-        const int L = lvl[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
         const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
@@ -468,72 +492,34 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r,
                 for (int c = 0; c < KT; ++c)
                     if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
             }
-        int32_t pk[BK_PFE];
-        double pm[BK_PFE];
-#pragma unroll
-        for (int u = 0; u < BK_PFE; ++u) {
-            const int64_t e = d0 + lane + 32 * u;
-            pk[u] = -1;
-            pm[u] = 0.0;
-            if (e < d1) { pk[u] = a.mcol[e]; pm[u] = (double)mv[e]; }
-        }
-        ok = bk_level_wait(done, L, epoch, lsz, lane, &a.S->err) && ok;
-#pragma unroll
-        for (int u = 0; u < BK_PFE; ++u) {
-            if (pk[u] >= 0) {
-                const double* row = e_new + (int64_t)pk[u] * K;
-#pragma unroll
-                for (int c = 0; c < KT; ++c)
-                    if (c < K) acc[c] = fma(pm[u], row[c], acc[c]);
-            }
-        }
-        for (int64_t e = d0 + lane + 32 * BK_PFE; e < d1; e += 32) {   // very long rows
-            const double* row = e_new + (int64_t)a.mcol[e] * K;
-            const double mk = (double)mv[e];
-#pragma unroll
-            for (int c = 0; c < KT; ++c)
-                if (c < K) acc[c] = fma(mk, row[c], acc[c]);
-        }
+        for (int64_t e = d0 + lane; e < d1; e += 32) bk_entry<MT, KT>(a, e_new, e, acc);
         const double tot = bk_reduce_scatter<KT>(acc, lane);
         if (writer) {
             const double dj = a.dinv[j];
             const int64_t at = j * K + my_col;
-            e_new[at] = identity ? e_old[at] - tot * dj : (r[at] - tot) * dj;
+            bk_stv(e_new + at, identity ? e_old[at] - tot * dj : (r[at] - tot) * dj);
         }
         __syncwarp();
-        if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (gw & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
     }
-    const unsigned any_bad = __ballot_sync(0xffffffffu, !ok);
-    if (lane == 0 && any_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
-// The same sweep for very long rows: a whole CTA takes a row (CTA b: schedule slots b, b + G,
-// ... in level order).  Thread t takes entries t, t + 256, ... of the row and keeps KT column
-// accumulators; warp 0 waits for the previous level and a block barrier releases the others;
-// each warp reduce-scatters its accumulators and the warps' partials are added in warp order.
-constexpr int BK_PFC = 2;
+// Very long rows: a whole CTA takes a row (CTA b: schedule slots b, b + G, ...); thread t takes
+// entries t, t + 256, ... with KT column accumulators; the warps' reduce-scattered partials are
+// added in warp order.
 template <typename MT, bool FWD, int KT>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r, const double* e_old,
                                                        double* e_new, int identity, int sweep_idx) {
     __shared__ double s_part[BK_T / 32][KT];
-    __shared__ int s_bad;
     if (a.S->done) return;
-    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
-    const unsigned long long epoch = (unsigned long long)a.S->napply * a.sweeps + tdir + 1;
-    unsigned long long* done = FWD ? a.done_f : a.done_b;
-    const int32_t* lvl = FWD ? a.lvl_f : a.lvl_b;
-    const int64_t* lsz = FWD ? a.lsize_f : a.lsize_b;
     const int32_t* sched = FWD ? a.sched_f : a.sched_b;
     const MT* mv = reinterpret_cast<const MT*>(a.mval);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int K = a.K;
     const bool other = !identity && e_old != nullptr;
     constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
+    (void)sweep_idx;
     for (int64_t slot = blockIdx.x; slot < a.n; slot += gridDim.x) {
         const int64_t j = sched[slot];
-        const int L = lvl[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
         const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
@@ -548,37 +534,7 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r
                 for (int c = 0; c < KT; ++c)
                     if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
             }
-        int32_t pk[BK_PFC];
-        double pm[BK_PFC];
-#pragma unroll
-        for (int u = 0; u < BK_PFC; ++u) {
-            const int64_t e = d0 + tid + BK_T * u;
-            pk[u] = -1;
-            pm[u] = 0.0;
-            if (e < d1) { pk[u] = a.mcol[e]; pm[u] = (double)mv[e]; }
-        }
-        if (wid == 0) {
-            const bool ok = bk_level_wait(done, L, epoch, lsz, lane, &a.S->err);
-            if (!ok && lane == 0) s_bad = 1;
-            __threadfence();
-        }
-        __syncthreads();   // the level's rows are visible to every warp of the CTA
-#pragma unroll
-        for (int u = 0; u < BK_PFC; ++u) {
-            if (pk[u] >= 0) {
-                const double* row = e_new + (int64_t)pk[u] * K;
-#pragma unroll
-                for (int c = 0; c < KT; ++c)
-                    if (c < K) acc[c] = fma(pm[u], row[c], acc[c]);
-            }
-        }
-        for (int64_t e = d0 + tid + BK_T * BK_PFC; e < d1; e += BK_T) {   // longer rows
-            const double* row = e_new + (int64_t)a.mcol[e] * K;
-            const double mk = (double)mv[e];
-#pragma unroll
-            for (int c = 0; c < KT; ++c)
-                if (c < K) acc[c] = fma(mk, row[c], acc[c]);
-        }
+        for (int64_t e = d0 + tid; e < d1; e += BK_T) bk_entry<MT, KT>(a, e_new, e, acc);
         const double tot = bk_reduce_scatter<KT>(acc, lane);
         if ((lane & ((1 << SH) - 1)) == 0) s_part[wid][lane >> SH] = tot;
         __syncthreads();
@@ -588,15 +544,10 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r
             for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][tid];
             const double dj = a.dinv[j];
             const int64_t at = j * K + tid;
-            e_new[at] = identity ? e_old[at] - sum * dj : (r[at] - sum) * dj;
-        }
-        if (wid == 0) {
-            __syncwarp();
-            if (lane == 0) bk_red_release_add_u64(&done[(int64_t)L * LVL_WORDS + (blockIdx.x & (LVL_SUB - 1)) * LVL_STRIDE], 1ull);
+            bk_stv(e_new + at, identity ? e_old[at] - sum * dj : (r[at] - sum) * dj);
         }
         __syncthreads();   // s_part is reused by the next row
     }
-    if (tid == 0 && s_bad) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 }
 
 // rho'_c = g_c^T z_c; the last block sets beta_c = rho'_c / rho_c (0 on the first call) and
@@ -723,6 +674,9 @@ static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const doubl
             grids[kern] = grid;
         }
     }
+    const int64_t cnt = a.n * a.K;   // every value of e_new starts as the empty marker
+    k_bk_fill_empty<<<(unsigned)std::min<int64_t>((cnt + BK_T - 1) / BK_T, 152 * 8), BK_T, 0, st>>>(enew, cnt);
+    count_launch();
     BkArgs av = a;
     void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &idx};
     LSQ_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BK_T), params, 0, st));
@@ -775,7 +729,6 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     const size_t o_S = take(sizeof(BkState)), o_vT = take(es * nnz),
                  o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16), o_vec = take(8 * (size_t)nK * 10),
                  o_q = take(8 * (size_t)m * K), o_b = take(B ? 8 * (size_t)m * K : 16),
-                 o_done = take(8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b)),
                  o_part = take(8 * (size_t)2 * grid_cap * K), o_n2 = take(8 * 2 * BK_MAX);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
@@ -795,7 +748,6 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
     a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
-    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
     a.sweeps = P->sweeps;
     a.y = vec; a.g = vec + nK; a.z = vec + 2 * nK; a.p = vec + 3 * nK; a.pt = vec + 4 * nK;
     a.w = vec + 5 * nK; a.e0 = vec + 6 * nK; a.e1 = vec + 7 * nK; a.h = vec + 8 * nK;
@@ -878,7 +830,6 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         return LSQ_OK;
     };
     LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(BkState), st));
-    LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));
     LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)nK, st));
     if (Hcols) {
         k_bk_to_rows<<<bk_grid(nK, 4096), BK_T, 0, st>>>(Hcols, ldb, n, K, a.h);

@@ -70,6 +70,8 @@ struct BkArgs {
     const int64_t* lsize_f;
     const int64_t* lsize_b;
     int sweeps;
+    unsigned* rflag_f;        // CTA-per-row form: sweep epoch at which each row's values were written
+    unsigned* rflag_b;
     double *y, *g, *z, *p, *pt, *w, *q, *e0, *e1, *h;
     double* part;             // per-block partials, [blocks][K] (x2 for the norms)
     BkState* S;
@@ -295,6 +297,14 @@ __global__ void k_bk_fill_empty(double* e, int64_t cnt) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         u[t] = BK_EMPTY;
 }
+__device__ __forceinline__ unsigned bk_ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void bk_st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long bk_ldv(const double* p) {
     unsigned long long v;
     asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -505,19 +515,25 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r,
 
 // Very long rows: a whole CTA takes a row (CTA b: schedule slots b, b + G, ...); thread t takes
 // entries t, t + 256, ... with KT column accumulators; the warps' reduce-scattered partials are
-// added in warp order.
+// added in warp order.  Here a row's K values are published by one flag per row (the sweep's
+// epoch, release) after they are written, so a reader polls one flag per dependency (acquire,
+// batched, bounded) and then loads the values; the flags are cumulative over the solve, so
+// nothing is reset between sweeps.
+constexpr int BK_PFC = 4;
 template <typename MT, bool FWD, int KT>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r, const double* e_old,
                                                        double* e_new, int identity, int sweep_idx) {
     __shared__ double s_part[BK_T / 32][KT];
     if (a.S->done) return;
+    const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
+    const unsigned epoch = (unsigned)((unsigned long long)a.S->napply * a.sweeps + tdir + 1);
+    unsigned* flag = FWD ? a.rflag_f : a.rflag_b;
     const int32_t* sched = FWD ? a.sched_f : a.sched_b;
     const MT* mv = reinterpret_cast<const MT*>(a.mval);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int K = a.K;
     const bool other = !identity && e_old != nullptr;
     constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
-    (void)sweep_idx;
     for (int64_t slot = blockIdx.x; slot < a.n; slot += gridDim.x) {
         const int64_t j = sched[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
@@ -534,17 +550,59 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r
                 for (int c = 0; c < KT; ++c)
                     if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
             }
-        for (int64_t e = d0 + tid; e < d1; e += BK_T) bk_entry<MT, KT>(a, e_new, e, acc);
+        for (int64_t base = d0 + tid; base < d1; base += BK_T * BK_PFC) {
+            int32_t kk[BK_PFC];
+            double mm[BK_PFC];
+            unsigned f[BK_PFC];
+#pragma unroll
+            for (int u = 0; u < BK_PFC; ++u) {
+                const int64_t e = base + (int64_t)BK_T * u;
+                kk[u] = -1;
+                mm[u] = 0.0;
+                if (e < d1) { kk[u] = a.mcol[e]; mm[u] = (double)mv[e]; }
+            }
+#pragma unroll
+            for (int u = 0; u < BK_PFC; ++u) f[u] = kk[u] >= 0 ? bk_ld_acquire_u32(flag + kk[u]) : epoch;
+            unsigned polls = 0, ns = 32;
+            while (true) {
+                bool missing = false;
+#pragma unroll
+                for (int u = 0; u < BK_PFC; ++u) missing = missing || f[u] < epoch;
+                if (!missing) break;
+                ++polls;
+                if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+                    atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+                    break;
+                }
+                if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+#pragma unroll
+                for (int u = 0; u < BK_PFC; ++u)
+                    if (f[u] < epoch) f[u] = bk_ld_acquire_u32(flag + kk[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < BK_PFC; ++u) {
+                if (kk[u] >= 0) {
+                    const double* row = e_new + (int64_t)kk[u] * K;
+#pragma unroll
+                    for (int c = 0; c < KT; ++c)
+                        if (c < K) acc[c] = fma(mm[u], __ldcg(row + c), acc[c]);
+                }
+            }
+        }
         const double tot = bk_reduce_scatter<KT>(acc, lane);
         if ((lane & ((1 << SH) - 1)) == 0) s_part[wid][lane >> SH] = tot;
         __syncthreads();
-        if (tid < K) {
-            double sum = 0.0;
+        if (wid == 0) {
+            if (lane < K) {
+                double sum = 0.0;
 #pragma unroll
-            for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][tid];
-            const double dj = a.dinv[j];
-            const int64_t at = j * K + tid;
-            bk_stv(e_new + at, identity ? e_old[at] - sum * dj : (r[at] - sum) * dj);
+                for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][lane];
+                const double dj = a.dinv[j];
+                const int64_t at = j * K + lane;
+                e_new[at] = identity ? e_old[at] - sum * dj : (r[at] - sum) * dj;
+            }
+            __syncwarp();
+            if (lane == 0) bk_st_release_u32(flag + j, epoch);
         }
         __syncthreads();   // s_part is reused by the next row
     }
@@ -729,7 +787,8 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     const size_t o_S = take(sizeof(BkState)), o_vT = take(es * nnz),
                  o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16), o_vec = take(8 * (size_t)nK * 10),
                  o_q = take(8 * (size_t)m * K), o_b = take(B ? 8 * (size_t)m * K : 16),
-                 o_part = take(8 * (size_t)2 * grid_cap * K), o_n2 = take(8 * 2 * BK_MAX);
+                 o_part = take(8 * (size_t)2 * grid_cap * K), o_n2 = take(8 * 2 * BK_MAX),
+                 o_flag = take(4 * (size_t)2 * n);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
     char* base = sc.as<char>();
@@ -749,6 +808,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
     a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
     a.sweeps = P->sweeps;
+    a.rflag_f = (unsigned*)(base + o_flag); a.rflag_b = a.rflag_f + n;
     a.y = vec; a.g = vec + nK; a.z = vec + 2 * nK; a.p = vec + 3 * nK; a.pt = vec + 4 * nK;
     a.w = vec + 5 * nK; a.e0 = vec + 6 * nK; a.e1 = vec + 7 * nK; a.h = vec + 8 * nK;
     double* tmpv = vec + 9 * nK;
@@ -830,6 +890,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         return LSQ_OK;
     };
     LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(BkState), st));
+    LSQ_CUDA(cudaMemsetAsync(a.rflag_f, 0, 4 * (size_t)2 * n, st));
     LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)nK, st));
     if (Hcols) {
         k_bk_to_rows<<<bk_grid(nK, 4096), BK_T, 0, st>>>(Hcols, ldb, n, K, a.h);

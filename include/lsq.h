@@ -271,12 +271,12 @@ LSQ_API lsq_status lsq_pcg_adjoint(const lsq_matrix* A, const lsq_precond* P, co
  *   X, ldx     device double, k solutions, column c at X + c*ldx (ldx >= n) (output)
  * Every pointer is borrowed and must stay valid for the life of the plan.
  *
- * lsq_batch_create   copies the problem table to the device, assigns problems to thread-block
- *                    clusters (largest first, each to the least loaded cluster), allocates
- *                    the workspace.  1 <= k <= 16.  o: tol, maxit, max_outer, inner_tol.
+ * lsq_batch_create   copies the problem table to the device with the problems ordered largest
+ *                    first (thread-block clusters take them from a queue in that order),
+ *                    allocates the workspace.  1 <= k <= 16.  o: tol, maxit, max_outer, inner_tol.
  *                    Synchronises the stream.  *out is library-owned.
- * lsq_batch_solve    one launch, stream-ordered, no host synchronisation and no allocation:
- *                    can be captured in a CUDA graph.  Results go to the plan's device
+ * lsq_batch_solve    a memset of the queue counter and one launch, stream-ordered, no host
+ *                    synchronisation and no allocation: can be captured in a CUDA graph.  Results go to the plan's device
  *                    status table.
  * lsq_batch_autotune times lsq_batch_solve for each cluster size that fits (1, 2, 4, 8 and,
  *                    where the device allows it, 16 CTAs per problem) and keeps the fastest;

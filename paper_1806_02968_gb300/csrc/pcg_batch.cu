@@ -2,8 +2,8 @@
 // FP32 values, k <= 16 right-hand sides each), all solved in ONE kernel launch.
 //
 // Each problem is solved by one thread-block cluster of C CTAs (C = 1..16, picked by the
-// autotuner).  The host assigns problems to clusters ahead of time (largest first, each to the
-// least loaded cluster), so clusters never wait on one another; the C CTAs of a cluster split
+// autotuner).  Clusters take problems from a queue, largest first, and never wait on one
+// another; the C CTAs of a cluster split
 // the problem's rows and meet at hardware cluster barriers, exchanging partial results through
 // distributed shared memory.  Per iteration (K = k columns advanced together, each with its
 // own alpha, beta, rho and convergence mask):
@@ -334,6 +334,7 @@ struct BtState {
     double qq[16];           // this CTA's ||Q||^2 per column
     int32_t active[16], iters[16], conv[16], broke[16], outer[16], dirty[16];
     int32_t any;
+    int32_t next;            // rank 0: the queue position this cluster took
 };
 static_assert(sizeof(BtState) <= 32 * 32 * 8, "state does not fit its shared-memory slot");
 
@@ -632,19 +633,24 @@ __device__ void bt_solve_problem(cg::cluster_group& cl, const BatchProb& P, int 
     cl.sync();   // the next problem reuses every shared-memory buffer
 }
 
-// One launch for the whole batch: cluster q solves plist[pstart[q] .. pstart[q+1]) in order.
+// One launch for the whole batch.  plist holds the problems largest first; each cluster takes
+// the next one from a queue (rank 0 increments *queue, the cluster reads its value through
+// distributed shared memory), so the clusters stay busy until the queue is empty.  The queue
+// counter is zeroed before every launch.
 template <int KC>
-__global__ void __launch_bounds__(BT, 1) k_pcg_batch(const BatchProb* probs, const int32_t* plist,
-                                                     const int32_t* pstart, int nclusters, int k, BatchOut* out,
-                                                     double tol, double inner_tol, int maxit, int max_outer) {
+__global__ void __launch_bounds__(BT, 1) k_pcg_batch(const BatchProb* probs, const int32_t* plist, int count,
+                                                     int* queue, int k, BatchOut* out, double tol,
+                                                     double inner_tol, int maxit, int max_outer) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cl = cg::this_cluster();
-    const unsigned q = bt_cluster_id();
-    if ((int)q < nclusters) {   // uniform over the cluster
-        for (int i = pstart[q]; i < pstart[q + 1]; ++i) {
-            const int pid = plist[i];
-            bt_solve_problem<KC>(cl, probs[pid], pid, k, out, tol, inner_tol, maxit, max_outer, smem);
-        }
+    BtState* S = reinterpret_cast<BtState*>(smem + BLayout<KC>::st);
+    while (true) {
+        if (cl.block_rank() == 0 && threadIdx.x == 0) S->next = atomicAdd(queue, 1);
+        cl.sync();
+        const int at = cl.map_shared_rank(S, 0)->next;   // the same value in every CTA
+        if (at >= count) break;
+        const int pid = plist[at];
+        bt_solve_problem<KC>(cl, probs[pid], pid, k, out, tol, inner_tol, maxit, max_outer, smem);
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
@@ -663,9 +669,9 @@ struct lsq_batch {
     lsq::BatchProb* dprobs = nullptr;
     lsq::BatchOut* dout = nullptr;
     double* ws = nullptr;
-    int32_t* dplist = nullptr;
-    int32_t* dpstart = nullptr;
-    int max_clusters = 0;               // capacity of dpstart
+    int32_t* dplist = nullptr;          // problems, largest first
+    int* dqueue = nullptr;              // queue position, zeroed before each launch
+    int max_clusters = 0;
     int cluster = 0, nclusters = 0;     // current plan
 };
 
@@ -720,30 +726,6 @@ static lsq_status bt_max_clusters(int kc, int C, int* out) {
     return LSQ_OK;
 }
 
-// Largest problem first, each to the cluster with the least work so far (ties: lowest index).
-static void bt_assign(const std::vector<int64_t>& cost, int nclusters, std::vector<int32_t>& plist,
-                      std::vector<int32_t>& pstart) {
-    const int64_t count = (int64_t)cost.size();
-    std::vector<int32_t> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-    std::vector<int64_t> load(nclusters, 0);
-    std::vector<std::vector<int32_t>> lists(nclusters);
-    for (int32_t pid : order) {
-        int best = 0;
-        for (int q = 1; q < nclusters; ++q)
-            if (load[q] < load[best]) best = q;
-        lists[best].push_back(pid);
-        load[best] += cost[pid];
-    }
-    plist.clear();
-    pstart.assign(1, 0);
-    for (int q = 0; q < nclusters; ++q) {
-        plist.insert(plist.end(), lists[q].begin(), lists[q].end());
-        pstart.push_back((int32_t)plist.size());
-    }
-}
-
 static lsq_status bt_set_cluster(lsq_batch* b, int C) {
     int nc = 0;
     lsq_status r = bt_max_clusters(b->kc, C, &nc);
@@ -753,11 +735,6 @@ static lsq_status bt_set_cluster(lsq_batch* b, int C) {
         return LSQ_ERR_UNSUPPORTED;
     }
     nc = (int)std::min<int64_t>(nc, std::min<int64_t>(b->count, b->max_clusters));
-    std::vector<int32_t> plist, pstart;
-    bt_assign(b->cost, nc, plist, pstart);
-    LSQ_CUDA(cudaMemcpyAsync(b->dplist, plist.data(), 4 * plist.size(), cudaMemcpyHostToDevice, b->stream));
-    LSQ_CUDA(cudaMemcpyAsync(b->dpstart, pstart.data(), 4 * pstart.size(), cudaMemcpyHostToDevice, b->stream));
-    LSQ_CUDA(cudaStreamSynchronize(b->stream));
     b->cluster = C;
     b->nclusters = nc;
     return LSQ_OK;
@@ -779,11 +756,12 @@ static cudaError_t bt_launch(lsq_batch* b, cudaStream_t st) {
     cfg.numAttrs = 1;
     const double inner = b->o.inner_tol > 0 ? b->o.inner_tol : 0.0;
     return cudaLaunchKernelEx(&cfg, k_pcg_batch<KC>, (const BatchProb*)b->dprobs, (const int32_t*)b->dplist,
-                              (const int32_t*)b->dpstart, b->nclusters, b->k, b->dout, b->o.tol, inner,
+                              (int)b->count, b->dqueue, b->k, b->dout, b->o.tol, inner,
                               (int)b->o.maxit, (int)b->o.max_outer);
 }
 
 static lsq_status bt_solve(lsq_batch* b, cudaStream_t st) {
+    LSQ_CUDA(cudaMemsetAsync(b->dqueue, 0, sizeof(int), st));
     cudaError_t e;
     switch (b->kc) {
         case 1: e = bt_launch<1>(b, st); break;
@@ -843,7 +821,7 @@ extern "C" lsq_status lsq_batch_create(const lsq_batch_problem* probs, int64_t c
         cudaMalloc(&B->dout, sizeof(BatchOut) * count * k) != cudaSuccess ||
         cudaMalloc(&B->ws, 8 * ws_total) != cudaSuccess ||
         cudaMalloc(&B->dplist, 4 * count) != cudaSuccess ||
-        cudaMalloc(&B->dpstart, 4 * (size_t)(sms + 1)) != cudaSuccess) {
+        cudaMalloc(&B->dqueue, 256) != cudaSuccess) {
         cudaGetLastError();
         set_error("out of device memory for the batch plan");
         return fail(LSQ_ERR_NOMEM);
@@ -853,7 +831,12 @@ extern "C" lsq_status lsq_batch_create(const lsq_batch_problem* probs, int64_t c
         hp[i].ws = B->ws + off;
         off += 5 * (size_t)hp[i].npad * kc;
     }
+    std::vector<int32_t> order(count);   // largest first (ties: lower index first)
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
     if (cudaMemcpyAsync(B->dprobs, hp.data(), sizeof(BatchProb) * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(B->dplist, order.data(), 4 * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess ||
         cudaMemsetAsync(B->dout, 0, sizeof(BatchOut) * count * k, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("copying the batch table failed");
@@ -947,6 +930,6 @@ extern "C" void lsq_batch_destroy(lsq_batch* b) {
     cudaFree(b->dout);
     cudaFree(b->ws);
     cudaFree(b->dplist);
-    cudaFree(b->dpstart);
+    cudaFree(b->dqueue);
     delete b;
 }

@@ -460,12 +460,13 @@ def run_batch_workload(args):
     t3 = time.perf_counter()
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
+    Lc0 = api.launches()
     with torch.cuda.stream(stream):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             bt.solve(stream=stream)
     torch.cuda.synchronize()
-    L0 = api.launches()
+    kernels_per_replay = api.launches() - Lc0   # kernels in the captured graph
     for _ in range(args.warmup):
         g.replay()
     torch.cuda.synchronize()
@@ -518,7 +519,7 @@ def run_batch_workload(args):
                        "m_range": [1024, 16384], "n_range": [32, 256], "tol": args.tol,
                        "A_bytes": int(sum(T.numel() * 4 for T, _, _, _ in probs)), "cluster": cluster,
                        "l2": "A (about the L2 size) stays resident across replays"},
-            "gpu_launches": (api.launches() - L0) // max(1, args.warmup + args.steps),
+            "gpu_launches": kernels_per_replay * args.steps,
             "roofline": {"bound": "alu", "achieved": flops / (solve_ms / 1e3) / 1e12,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops / (solve_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,

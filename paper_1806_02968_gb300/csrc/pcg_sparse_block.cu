@@ -246,46 +246,15 @@ __global__ void __launch_bounds__(BK_T) k_bk_normal_fused(BkArgs a, const double
         for (int64_t j = grp; j < a.n; j += ngrp) {
             double t = 0.0;
             const int64_t eend = a.atptr[j + 1];
-            // 8 column entries at a time, each stage's loads issued together: row indices,
-            // row bounds, the rows' first two entries, their x values
-            for (int64_t e = a.atptr[j]; e < eend; e += 8) {
-                int64_t ii[8], ra[8], rb[8];
-                double av[8], q[8];
-                int32_t c0[8], c1[8];
-                double v0[8], v1[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const bool ok = e + u < eend;
-                    ii[u] = ok ? a.atrow[e + u] : -1;
-                    av[u] = ok ? Val<DT>::load(a.valsT, e + u) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    ra[u] = ii[u] >= 0 ? a.row_ptr[ii[u]] : 0;
-                    rb[u] = ii[u] >= 0 ? a.row_ptr[ii[u] + 1] : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    c0[u] = ra[u] < rb[u] ? a.col_idx[ra[u]] : 0;
-                    v0[u] = ra[u] < rb[u] ? Val<DT>::load(a.vals, ra[u]) : 0.0;
-                    c1[u] = ra[u] + 1 < rb[u] ? a.col_idx[ra[u] + 1] : 0;
-                    v1[u] = ra[u] + 1 < rb[u] ? Val<DT>::load(a.vals, ra[u] + 1) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    double qv = 0.0;
-                    if (ra[u] < rb[u]) qv = v0[u] * x[(int64_t)c0[u] * K + c];
-                    if (ra[u] + 1 < rb[u]) qv = fma(v1[u], x[(int64_t)c1[u] * K + c], qv);
-                    q[u] = qv;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (ii[u] < 0) continue;
-                    for (int64_t e2 = ra[u] + 2; e2 < rb[u]; ++e2)   // longer rows
-                        q[u] = fma(Val<DT>::load(a.vals, e2), x[(int64_t)a.col_idx[e2] * K + c], q[u]);
-                    t = fma(av[u], q[u], t);
-                    if (ra[u] < rb[u] && c0[u] == j) qq = fma(q[u], q[u], qq);
-                }
+            for (int64_t e = a.atptr[j]; e < eend; ++e) {
+                const int64_t i = a.atrow[e];
+                const double aij = Val<DT>::load(a.valsT, e);
+                const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
+                double q = 0.0;
+                for (int64_t e2 = r0; e2 < r1; ++e2)
+                    q = fma(Val<DT>::load(a.vals, e2), x[(int64_t)a.col_idx[e2] * K + c], q);
+                t = fma(aij, q, t);
+                if (a.col_idx[r0] == j) qq = fma(q, q, qq);
             }
             out[j * K + c] = t * a.inv_d[j];
         }

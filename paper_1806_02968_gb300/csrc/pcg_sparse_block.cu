@@ -227,43 +227,6 @@ __global__ void __launch_bounds__(BK_T) k_bk_cols(BkArgs a, int use_res, double*
     }
 }
 
-// w = D^{-1} A^T (A x) in ONE pass over the columns of A, for matrices with very short rows
-// (graph incidence: 2 entries): each column entry (i, a_ij) recomputes q_i = A_i x from row i
-// instead of reading a stored q, so the m x K vector q is neither written nor read back.
-// ||q||^2 = p^T w is summed once per row, by the row's first column; the last block leaves
-// the column sums in S->pw.  A group of GK lanes takes a column; lane c handles column c.
-template <int DT>
-__global__ void __launch_bounds__(BK_T) k_bk_normal_fused(BkArgs a, const double* x, double* out) {
-    __shared__ double sh[BK_T];
-    if (a.S->done) return;
-    const int c = threadIdx.x & (a.GK - 1);
-    const bool col_ok = c < a.K;
-    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / a.GK;
-    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / a.GK;
-    const int K = a.K;
-    double qq = 0.0;
-    if (col_ok)
-        for (int64_t j = grp; j < a.n; j += ngrp) {
-            double t = 0.0;
-            const int64_t eend = a.atptr[j + 1];
-            for (int64_t e = a.atptr[j]; e < eend; ++e) {
-                const int64_t i = a.atrow[e];
-                const double aij = Val<DT>::load(a.valsT, e);
-                const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
-                double q = 0.0;
-                for (int64_t e2 = r0; e2 < r1; ++e2)
-                    q = fma(Val<DT>::load(a.vals, e2), x[(int64_t)a.col_idx[e2] * K + c], q);
-                t = fma(aij, q, t);
-                if (a.col_idx[r0] == j) qq = fma(q, q, qq);
-            }
-            out[j * K + c] = t * a.inv_d[j];
-        }
-    bk_block_partials(qq, a.K, a.GK, a.part + (int64_t)blockIdx.x * a.K, sh);
-    if (!bk_last_block(&a.S->arrive[0])) return;
-    bk_total(a.part, gridDim.x, a.K, sh);
-    if ((int)threadIdx.x < a.K) a.S->pw[threadIdx.x] = sh[threadIdx.x];
-}
-
 // alpha_c = rho_c / p_c^T w_c (0 for frozen columns), y += alpha p, g -= alpha w.  The last
 // block sums ||g||^2, counts the iteration of every active column and freezes the columns
 // that met the tolerance or maxit; S->done once none is left.
@@ -869,8 +832,6 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         count_launch();
     }
     const unsigned grows = bk_grid(m * GK, grid_cap), gcols = bk_grid(n * GK, grid_cap), gvec = bk_grid(n * GK, 152 * 4);
-    // rows of at most ~2 entries (graph incidence): one fused pass over the columns
-    const bool fused = nnz <= 2 * m + m / 8;
     auto rows = [&](int mode, int use_res, const double* x) {
         if (use_res && res64) k_bk_rows<LSQ_F64><<<grows, BK_T, 0, st>>>(a, mode, 1, x);
         else k_bk_rows<DT><<<grows, BK_T, 0, st>>>(a, mode, 0, x);
@@ -999,13 +960,8 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         BkState hs{};
         while (true) {
             for (int b = 0; b < 8; ++b) {
-                if (fused) {
-                    k_bk_normal_fused<DT><<<gcols, BK_T, 0, st>>>(a, a.pt, a.w);
-                    count_launch();
-                } else {
-                    rows(0, 0, a.pt);
-                    cols(0, a.w);
-                }
+                rows(0, 0, a.pt);
+                cols(0, a.w);
                 k_bk_update<<<gvec, BK_T, 0, st>>>(a);
                 precond();
                 k_bk_gz<<<gvec, BK_T, 0, st>>>(a, 0);

@@ -94,7 +94,8 @@ constexpr int SP_T = 256;
 enum { SPM_MATVEC = 0, SPM_RHS = 1, SPM_RESID = 2 };
 
 // q_i = sum_e a_e x_{col e} (x = D^{-1} p or D^{-1} y), or b_i, or b_i - that.  A group of
-// LPR lanes (a power of two, about the mean row length) takes a row.
+// LPR lanes (a power of two, about the mean row length) takes 4 consecutive rows per step, so
+// that the loads of 4 rows are in flight together; each row sums its entries in a fixed order.
 template <int DT>
 __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_res, const double* x) {
     __shared__ double sh[40];
@@ -105,18 +106,30 @@ __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_re
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
     const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / L;
     double qq = 0.0;
-    for (int64_t i0 = 0; i0 < a.m; i0 += ngrp) {
-        const int64_t i = i0 + grp;
-        double dot = 0.0;
-        if (i < a.m && mode != SPM_RHS) {
-            const int64_t e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
-            for (int64_t e = e0 + sub; e < e1; e += L) dot = fma(Val<DT>::load(vals, e), x[a.col_idx[e]], dot);
+    for (int64_t i0 = grp * 4; i0 < a.m; i0 += ngrp * 4) {
+        int64_t rp[5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) rp[r] = a.row_ptr[min(i0 + r, a.m)];
+        double dot[4] = {0.0, 0.0, 0.0, 0.0};
+        if (mode != SPM_RHS) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                for (int64_t e = rp[r] + sub; e < rp[r + 1]; e += L)
+                    dot[r] = fma(Val<DT>::load(vals, e), x[a.col_idx[e]], dot[r]);
         }
-        for (int o = L >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (i < a.m && sub == 0) {
-            const double q = mode == SPM_MATVEC ? dot : (mode == SPM_RHS ? a.b[i] : a.b[i] - dot);
-            a.q[i] = q;
-            qq = fma(q, q, qq);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            for (int o = L >> 1; o > 0; o >>= 1) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], o);
+        if (sub == 0) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t i = i0 + r;
+                if (i < a.m) {
+                    const double q = mode == SPM_MATVEC ? dot[r] : (mode == SPM_RHS ? a.b[i] : a.b[i] - dot[r]);
+                    a.q[i] = q;
+                    qq = fma(q, q, qq);
+                }
+            }
         }
     }
     const double t = block_sum(qq, sh);

@@ -172,8 +172,11 @@ def test_bad_arguments(lsq):
     with pytest.raises(lsq.L.LsqError) as e:
         lsq.lsq_pcg_solve(Mx, P, torch.zeros(99, dtype=torch.float64, device="cuda"))
     assert e.value.code == 1
-    with pytest.raises(lsq.L.LsqError):
-        lsq.lsq_build_precond(Mx, idx, p, d, lsq.opts(sweeps=0))
+    # sweeps = 0 is the CG comparison method; negative and above 64 are rejected
+    for bad in (-1, 65):
+        with pytest.raises(lsq.L.LsqError) as e:
+            lsq.lsq_build_precond(Mx, idx, p, d, lsq.opts(sweeps=bad))
+        assert e.value.code == 1
 
 
 @pytest.mark.parametrize("with_f64", [True, False])

@@ -407,6 +407,14 @@ def run_sparse_workload(args):
                "relres_true_max": float(np.max(info.relres_true)), "nnz_A": int(mat["row_ptr"][-1]),
                "nnz_M": int(info.nnz_M), "levels": int(info.levels), "s": int(info.s)}
     tot = res["sample_s"] + res["build_s"] + res["solve_s"] + res.get("adjoint_s", 0.0)
+    # solve-level HBM rate: per iteration, A read twice (row and column passes) with its indices,
+    # the dependency side of M read once per sweep (2 sweeps), and ~12 n-vector passes per column
+    it = max(1, int(np.max(info.iters)))
+    es = 4 if dt == "f32" else 8
+    nnz_a, nnz_m = int(mat["row_ptr"][-1]), int(info.nnz_M)
+    per_iter = 2 * nnz_a * (es + 4) + 8 * (mat["m"] + 1) + nnz_m * (es + 4) + 12 * 8 * mat["n"] * k
+    res["solve_hbm_gbs"] = it * per_iter / res["solve_s"] / 1e9
+    res["solve_hbm_frac_of_measured"] = res["solve_hbm_gbs"] / peaks()["hbm_gbs"]
     line = {"metric": METRIC, "value": k / tot, "unit": "solves/s (right-hand sides)", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3, "higher_is_better": True,
             "dtype": dt + ("+f64" if dt == "f32" else ""), "data": "synthetic",

@@ -10,7 +10,7 @@ from helpers import rel
 pytestmark = pytest.mark.gpu
 
 
-def _problem(lsq, mat, seed, k, noise, pad_nan=True):
+def _problem(lsq, mat, seed, k, noise, pad_nan=True, pdt=1):
     """FP32 A stored with a leading dimension padded to a multiple of 4 (NaN in the
     padding, which the batch must never use), its preconditioner and k right-hand sides."""
     A64 = np.asarray(mat["A"])
@@ -19,7 +19,7 @@ def _problem(lsq, mat, seed, k, noise, pad_nan=True):
     T = torch.full((m, ld), float("nan") if pad_nan else 0.0, dtype=torch.float32, device="cuda")
     T[:, :n] = torch.from_numpy(A64).float().cuda()
     Mx = lsq.Matrix(T[:, :n])
-    o = lsq.opts(seed=seed, precond_dtype=1)
+    o = lsq.opts(seed=seed, precond_dtype=pdt)
     idx, p, d = lsq.lsq_sample_rows(Mx, o)
     P = lsq.lsq_build_precond(Mx, idx, p, d, o)
     seen = {"kind": "dense", "A": T[:, :n].double().cpu().numpy()}
@@ -48,10 +48,12 @@ def _check_against_oracle(orc, pr, X, info, tol, cols):
         assert abs(raw - info.relres_raw[c]) <= 1e-3 * raw + 1e-13
 
 
-def test_batch_uneven_matches_oracle(lsq, orc):
+@pytest.mark.parametrize("pdt", [1, 0])
+def test_batch_uneven_matches_oracle(lsq, orc, pdt):
+    """pdt: the SGS operator stored in FP32 (1) or FP64 (0)."""
     mats = W.uneven_dense_batch(10, (300, 6000), (5, 200), 51)
     k = 3
-    prs = [_problem(lsq, mt, 700 + i, k, 1e-3) for i, mt in enumerate(mats)]
+    prs = [_problem(lsq, mt, 700 + i, k, 1e-3, pdt=pdt) for i, mt in enumerate(mats)]
     o = _opts(lsq)
     bt = lsq.Batch([(pr["T"], pr["n"], pr["P"], pr["B"]) for pr in prs], o)
     bt.solve()

@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_re
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
     const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / L;
     double qq = 0.0;
-    for (int64_t i0 = grp * 4; i0 < a.m; i0 += ngrp * 4) {
+    // the trip count is the same for every lane of a warp (the shuffles below need all 32)
+    for (int64_t base = 0; base < a.m; base += ngrp * 4) {
+        const int64_t i0 = base + grp * 4;
         int64_t rp[5];
 #pragma unroll
         for (int r = 0; r < 5; ++r) rp[r] = a.row_ptr[min(i0 + r, a.m)];

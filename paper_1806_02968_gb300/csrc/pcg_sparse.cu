@@ -52,10 +52,6 @@ struct SpArgs {
     const int64_t* loff_b;
     int64_t one_f, one_b;       // level count when that direction runs in one CTA, else 0
     const int32_t* lvl_b;
-    const int64_t* lsize_f;     // rows per level
-    const int64_t* lsize_b;
-    unsigned long long* done_f; // rows finished per level, cumulative over the sweeps of a solve
-    unsigned long long* done_b;
     int lpr, lpc;               // lanes per row of A, lanes per column of A (powers of two <= 32)
     int sweeps;
     // vectors
@@ -560,7 +556,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
     size_t o_S = take(sizeof(SpState)), o_vT = take(es * nnz), o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16),
            o_vec = take(8 * (size_t)n * 10), o_q = take(8 * (size_t)m),
-           o_done = take(8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b)), o_part = take(8 * (size_t)(rblk + 2 * nblk)),
+           o_part = take(8 * (size_t)(rblk + 2 * nblk)),
            o_n2 = take(64);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
@@ -583,8 +579,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.w = vec + 5 * n; a.e0 = vec + 6 * n; a.e1 = vec + 7 * n; a.h = vec + 8 * n;
     double* tmpv = vec + 9 * n;
     a.q = (double*)(base + o_q);
-    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n); a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
-    a.done_f = (unsigned long long*)(base + o_done); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
+    a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n);
     auto lanes_for = [](double mean) { int L = 1; while (L < 32 && L < mean) L <<= 1; return L; };
     a.lpr = lanes_for((double)nnz / (double)m);
     a.lpc = lanes_for((double)nnz / (double)n);
@@ -653,7 +648,6 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     LSQ_CUDA(cudaEventRecord(ev0, st));
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(SpState), st));
-        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));
         LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)n, st));
         a.b = B ? B + c * ldb : nullptr;
         a.h_in = Hcols ? Hcols + c * ldb : nullptr;
@@ -783,8 +777,7 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     const int64_t n = P->n;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
-    size_t o_S = take(sizeof(SpState)), o_e = take(16 * (size_t)n),
-           o_f = take(8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b));
+    size_t o_S = take(sizeof(SpState)), o_e = take(16 * (size_t)n);
     Scratch sc;
     LSQ_CUDA(sc.alloc(off, st));
     char* base = sc.as<char>();
@@ -794,8 +787,7 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b; a.sweeps = P->sweeps;
     a.e0 = (double*)(base + o_e); a.e1 = a.e0 + n;
-    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n); a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
-    a.done_f = (unsigned long long*)(base + o_f); a.done_b = a.done_f + LVL_WORDS * SH->nlev_f;
+    a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n);
     a.S = (SpState*)(base + o_S);
     if (P->sweeps == 0) {
         LSQ_CUDA(cudaMemcpyAsync(e, r, 8 * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
@@ -804,7 +796,6 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     }
     for (int64_t c = 0; c < k; ++c) {
         LSQ_CUDA(cudaMemsetAsync(a.S, 0, sizeof(SpState), st));
-        LSQ_CUDA(cudaMemsetAsync(a.done_f, 0, 8 * (size_t)LVL_WORDS * (SH->nlev_f + SH->nlev_b), st));
         const double* rc = r + c * n;
         double* out = e + c * n;
         const double* eold = nullptr;

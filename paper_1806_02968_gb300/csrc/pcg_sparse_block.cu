@@ -65,10 +65,6 @@ struct BkArgs {
     const double* dinv;
     const int32_t* sched_f;
     const int32_t* sched_b;
-    const int32_t* lvl_f;
-    const int32_t* lvl_b;
-    const int64_t* lsize_f;
-    const int64_t* lsize_b;
     int sweeps;
     unsigned* rflag_f;        // CTA-per-row form: sweep epoch at which each row's values were written
     unsigned* rflag_b;
@@ -806,7 +802,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.mptr = SH->mptr; a.mcol = SH->mcol; a.mdiag = SH->mdiag;
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
-    a.lvl_f = SH->lvl_f; a.lvl_b = SH->lvl_b; a.lsize_f = SH->lsize_f; a.lsize_b = SH->lsize_b;
+   
     a.sweeps = P->sweeps;
     a.rflag_f = (unsigned*)(base + o_flag); a.rflag_b = a.rflag_f + n;
     a.y = vec; a.g = vec + nK; a.z = vec + 2 * nK; a.p = vec + 3 * nK; a.pt = vec + 4 * nK;

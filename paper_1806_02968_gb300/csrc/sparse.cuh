@@ -29,13 +29,6 @@ struct SparseHandle {
     int64_t* atperm = nullptr;
 };
 
-// Level completion counters of the sparse sweeps: LVL_SUB cumulative sub-counters per level,
-// each on its own 128-byte line (LVL_STRIDE 8-byte words apart) so that polls and updates
-// spread over L2 slices.
-constexpr int LVL_SUB = 32;
-constexpr int LVL_STRIDE = 16;
-constexpr int64_t LVL_WORDS = (int64_t)LVL_SUB * LVL_STRIDE;
-
 lsq_status scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* scratch, cudaStream_t st);
 lsq_status transpose_pattern(const int64_t* rptr, const int32_t* col, int64_t nr, int64_t nc, int64_t nnz,
                              int64_t* cptr, int32_t* trow, int64_t* tperm, cudaStream_t st);

@@ -47,11 +47,9 @@ struct SpArgs {
     const double* dinv;
     const int32_t* sched_f;
     const int32_t* sched_b;
-    const int32_t* lvl_f;       // level of each schedule slot
     const int64_t* loff_f;      // first slot of each level
     const int64_t* loff_b;
     int64_t one_f, one_b;       // level count when that direction runs in one CTA, else 0
-    const int32_t* lvl_b;
     int lpr, lpc;               // lanes per row of A, lanes per column of A (powers of two <= 32)
     int sweeps;
     // vectors

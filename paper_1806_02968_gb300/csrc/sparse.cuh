@@ -16,10 +16,6 @@ struct SparseHandle {
     // rows listed by forward / backward level (Gauss-Seidel dependency order)
     int32_t* sched_f = nullptr;
     int32_t* sched_b = nullptr;
-    int32_t* lvl_f = nullptr;     // level of each schedule slot
-    int32_t* lvl_b = nullptr;
-    int64_t* lsize_f = nullptr;   // rows per level
-    int64_t* lsize_b = nullptr;
     int64_t nlev_f = 0, nlev_b = 0;
     int64_t* loff_f = nullptr;    // first schedule slot of every level (nlev + 1 entries)
     int64_t* loff_b = nullptr;

@@ -465,19 +465,19 @@ __global__ void k_level_count(int64_t n, const int* lev1, unsigned long long* cn
 }
 // slot of every row: its level's offset plus a cursor (order inside a level is free)
 __global__ void k_level_scatter(int64_t n, const int* lev1, const int64_t* off, unsigned long long* cur,
-                                int32_t* sched, int32_t* lvl) {
+                                int32_t* sched) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const int l = lev1[j] - 1;
         const int64_t at = off[l] + (int64_t)atomicAdd(cur + l, 1ull);
         sched[at] = (int32_t)j;
-        lvl[at] = l;
     }
 }
 
-// One direction's schedule on the device: sched (n), lvl (n), lsize (levels), nlev.
+// One direction's schedule on the device: sched (n rows, level by level), loff (levels + 1
+// offsets into sched), nlev.
 template <bool FWD>
-static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sched, int32_t** lvl, int64_t** lsize,
-                                int64_t** loff, int64_t* nlev, cudaStream_t st) {
+static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sched, int64_t** loff, int64_t* nlev,
+                                cudaStream_t st) {
     int dev = 0, sms = 0, per = 0;
     LSQ_CUDA(cudaGetDevice(&dev));
     LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -502,21 +502,20 @@ static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sche
     if (hmax[1] != 0) { set_error("level schedule: a dependency wait timed out"); return LSQ_ERR_TIMEOUT; }
     const int64_t L = (int64_t)hmax[0] + 1;
     LSQ_CUDA(cudaMalloc(sched, 4 * (size_t)n));
-    LSQ_CUDA(cudaMalloc(lvl, 4 * (size_t)n));
-    LSQ_CUDA(cudaMalloc(lsize, 8 * (size_t)L));
     Scratch sc2;
     const int64_t nt = (L + SC_T - 1) / SC_T;   // scan_i64: out[0..L], ceil(L / 512) scratch
-    LSQ_CUDA(sc2.alloc(8 * (size_t)((L + 1) + L + nt + 1), st));
-    int64_t* off = sc2.as<int64_t>();
+    LSQ_CUDA(sc2.alloc(8 * (size_t)(L + (L + 1) + L + nt + 1), st));
+    int64_t* lsize = sc2.as<int64_t>();         // rows per level
+    int64_t* off = lsize + L;
     unsigned long long* cur = reinterpret_cast<unsigned long long*>(off + L + 1);
     int64_t* scan_scratch = off + (L + 1) + L;
-    LSQ_CUDA(cudaMemsetAsync(*lsize, 0, 8 * (size_t)L, st));
+    LSQ_CUDA(cudaMemsetAsync(lsize, 0, 8 * (size_t)L, st));
     LSQ_CUDA(cudaMemsetAsync(cur, 0, 8 * (size_t)L, st));
-    k_level_count<<<grid1(n), 256, 0, st>>>(n, lev1, reinterpret_cast<unsigned long long*>(*lsize));
+    k_level_count<<<grid1(n), 256, 0, st>>>(n, lev1, reinterpret_cast<unsigned long long*>(lsize));
     count_launch();
-    lsq_status r = scan_i64(*lsize, L, off, scan_scratch, st);
+    lsq_status r = scan_i64(lsize, L, off, scan_scratch, st);
     if (r != LSQ_OK) return r;
-    k_level_scatter<<<grid1(n), 256, 0, st>>>(n, lev1, off, cur, *sched, *lvl);
+    k_level_scatter<<<grid1(n), 256, 0, st>>>(n, lev1, off, cur, *sched);
     count_launch();
     LSQ_CUDA(cudaMalloc(loff, 8 * (size_t)(L + 1)));
     LSQ_CUDA(cudaMemcpyAsync(*loff, off, 8 * (size_t)(L + 1), cudaMemcpyDeviceToDevice, st));
@@ -636,9 +635,9 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
     LSQ_CUDA(cudaGetLastError());
     LSQ_CUDA(cudaStreamSynchronize(st));
     // 4. level schedules of the forward and backward sweeps (device)
-    r = device_levels<true>(S, n, &S->sched_f, &S->lvl_f, &S->lsize_f, &S->loff_f, &S->nlev_f, st);
+    r = device_levels<true>(S, n, &S->sched_f, &S->loff_f, &S->nlev_f, st);
     if (r != LSQ_OK) return r;
-    r = device_levels<false>(S, n, &S->sched_b, &S->lvl_b, &S->lsize_b, &S->loff_b, &S->nlev_b, st);
+    r = device_levels<false>(S, n, &S->sched_b, &S->loff_b, &S->nlev_b, st);
     if (r != LSQ_OK) return r;
     // 5. transposed pattern of A for the A^T q pass (values are gathered at solve time)
     LSQ_CUDA(cudaMalloc(&S->atptr, 8 * (size_t)(n + 1)));
@@ -660,8 +659,8 @@ lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p
 void free_sparse(SparseHandle* S) {
     if (!S) return;
     cudaFree(S->mptr); cudaFree(S->mcol); cudaFree(S->mval); cudaFree(S->mval32); cudaFree(S->dinv); cudaFree(S->mdiag);
-    cudaFree(S->sched_f); cudaFree(S->sched_b); cudaFree(S->lvl_f); cudaFree(S->lvl_b);
-    cudaFree(S->lsize_f); cudaFree(S->lsize_b); cudaFree(S->atptr); cudaFree(S->atrow);
+    cudaFree(S->sched_f); cudaFree(S->sched_b);
+    cudaFree(S->atptr); cudaFree(S->atrow);
     cudaFree(S->atperm); cudaFree(S->loff_f); cudaFree(S->loff_b);
     delete S;
 }

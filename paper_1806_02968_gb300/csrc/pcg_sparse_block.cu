@@ -802,7 +802,6 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.mptr = SH->mptr; a.mcol = SH->mcol; a.mdiag = SH->mdiag;
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b;
-   
     a.sweeps = P->sweeps;
     a.rflag_f = (unsigned*)(base + o_flag); a.rflag_b = a.rflag_f + n;
     a.y = vec; a.g = vec + nK; a.z = vec + 2 * nK; a.p = vec + 3 * nK; a.pt = vec + 4 * nK;

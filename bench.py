@@ -63,6 +63,29 @@ def dist_env():
     return world, rank, local
 
 
+# N > 1 runs N independent replicas (weak scaling): every rank solves its own problem with
+# no data-path collective; the ranks meet only at the barriers around the timed region and
+# in the max-over-ranks reduction of its duration.
+def replica_seeds(rank):
+    """Seeds of rank's problem: (matrix and right-hand side, row sampling)."""
+    return 2 + rank, 1002 + rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's timed-region duration, known to every rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, ms):
+    """Solves per second of the whole job: every rank's steps over the slowest rank's time."""
+    return world * steps / (ms / 1e3)
+
+
 class Clocks:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -173,8 +196,8 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    mat, xs, b = make_problem(args, 2, device_matmul=False)
-    seed = 1002
+    seed_base, seed = replica_seeds(0)
+    mat, xs, b = make_problem(args, seed_base, device_matmul=False)
     times = []
     # iterations of a full FP64 solve of the default workload, as measured on the GPU's FP64
     # path (105,426: the same textbook PCG as the oracle, another summation order)
@@ -213,7 +236,7 @@ def run_ours(args):
         dist.barrier()
     from paper_1806_02968_gb300 import api
 
-    seed_base = 2 + rank                     # independent replica per rank (weak scaling)
+    seed_base, seed_sample = replica_seeds(rank)
     mat, xs, b = make_problem(args, seed_base)
     m, n = mat["A"].shape
     A64 = torch.from_numpy(mat["A"]).cuda()
@@ -235,7 +258,7 @@ def run_ours(args):
             return api.Matrix(A32, vals_f64=Asrc), A32
         pairs = api.lsq_split_f64(Asrc)
         return api.Matrix(pairs, f32x2=True, vals_f64=Asrc), pairs
-    o = api.opts(seed=1002 + rank, tol=args.tol, maxit=args.maxit, precond_dtype=pdt, sweeps=args.sweeps,
+    o = api.opts(seed=seed_sample, tol=args.tol, maxit=args.maxit, precond_dtype=pdt, sweeps=args.sweeps,
                  inner_tol=args.inner_tol, max_outer=50)
     stream = torch.cuda.current_stream()
 
@@ -275,12 +298,9 @@ def run_ours(args):
     launches = api.launches() - L0
     ck = clocks.stop()
     ms = t_start.elapsed_time(t_end)
-    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms = float(tmax.item())
+    ms = max_over_ranks(ms, world, "cuda")
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, args.steps, ms)
 
     info = infos[-1]
     byts, flops = pcg_algorithmic(args, m, n, info, es, es_res, es_op)
@@ -330,7 +350,7 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        t_solve, t_setup, t_iter = cpu_oracle_sample(mat, b, 1002, int(info.iters[0]), args.cpu_iters)
+        t_solve, t_setup, t_iter = cpu_oracle_sample(mat, b, seed_sample, int(info.iters[0]), args.cpu_iters)
         cpu = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle setup (sampling, A_s^T A_s, SGS) on the full matrix "
                          f"({t_setup:.2f} s) + {args.cpu_iters} PCG iterations ({t_iter:.3f} s each), "

@@ -186,6 +186,25 @@ def test_sparse_block_maxit_and_two_sweeps(lsq, orc):
         assert rel(X3[c].cpu().numpy(), y / smp.d) <= 1e-10
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_sparse_bf16_values_match_oracle(lsq, orc, k):
+    """BF16 CSR values (k = 1: the one-column path; k = 3: the block path). Every value
+    widens exactly to FP64, so the solve is the FP64 method on the BF16-rounded matrix,
+    which is the matrix the oracle is given."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["sprand"](), 3001, dtype="bf16")
+    xs, b = W.rhs_for(seen, k, 1e-3, 29)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b if k > 1 else b[0]).cuda(), o)
+    X = X.cpu().numpy().reshape(k, -1)
+    kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
+    assert info.nnz_M == Mo.val.size
+    for c in range(k):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+        assert info.converged[c] == 1 and oi["converged"] == 1 and info.relres_true[c] <= o.tol
+        assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
+        assert _same_solution(seen, smp.d, X[c], y, b[c], o.tol)
+        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
+
+
 def test_sparse_block_f32_refinement(lsq, orc):
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["sprand"](), 8, dtype="f32", pdt=1, with_f64=True)
     o.max_outer = 30

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -60,3 +61,14 @@ def test_package_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.lower().replace("oracle-free", ""), f
+
+
+def test_missing_library_raises_instead_of_falling_back(tmp_path):
+    """Without liblsq.so the package refuses to run: there is no CPU or Python path."""
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1806_02968_gb300 import _lib\n"
+            "try:\n    _lib.load(%r)\nexcept RuntimeError as e:\n    print('raised', e)\n"
+            "else:\n    print('loaded')\n") % (ROOT, str(tmp_path / "liblsq.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("raised") and "is missing" in out.stdout

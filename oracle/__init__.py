@@ -23,13 +23,19 @@ _lock = threading.Lock()
 _lib = None
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2 with FMA contraction off (every product rounded once) into a shared library."""
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared",
+                           "-ffp-contract=off", "-fno-fast-math", "-o", out, src, "-lm"])
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FMA contraction) into oracle/_build/."""
+    """Compile the oracle into oracle/_build/ (when the source is newer than the library)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        compile_source(_SRC, tmp)
         os.replace(tmp, _SO)
     return _SO
 

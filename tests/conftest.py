@@ -32,7 +32,13 @@ def pytest_collection_modifyitems(config, items):
 @pytest.fixture(scope="session")
 def orc():
     import oracle
-    oracle.build()
+    mutant = os.environ.get("LSQ_ORACLE_MUTANT")
+    if mutant:
+        # a copy of the oracle with one planted mistake (tests/test_oracle_mutants.py):
+        # the pins run against it and must fail
+        oracle.build = lambda force=False: mutant
+    else:
+        oracle.build()
     return oracle
 
 

@@ -210,15 +210,32 @@ def test_sampled_normal_matrix_is_unbiased(orc):
 
 
 def test_unsampled_column_gets_unit_diagonal(orc):
-    A = np.zeros((10, 3))
+    """A column no drawn row touches has M_jj = 0; it becomes 1, the diagonal of the
+    normalised A^T A, and it is the only entry of its row and column.  Column 2 lives in
+    row 9 only; column 3 is all zero, so no seed can reach it.  Which columns the draws
+    miss is counted here by brute force from the drawn rows."""
+    A = np.zeros((10, 4))
     A[:5, 0] = 1.0
     A[5:, 1] = 2.0
-    A[9, 2] = 1e-30            # column 2 exists but is never drawn with these seeds/sizes
-    smp = orc.Sample({"kind": "dense", "A": A}, seed=1, s=4)
-    Mo = orc.SampledM(smp)
-    Md = Mo.dense()
-    if 9 not in smp.idx:
-        assert Md[2, 2] == 1.0 and Mo.n_fixed_diag == 1
+    A[9, 2] = 1e-30
+    mat = {"kind": "dense", "A": A}
+    seen_missed_2 = seen_hit_2 = False
+    for seed in range(1, 60):
+        smp = orc.Sample(mat, seed=seed, s=4)
+        drawn = np.unique(smp.idx)
+        missed = [j for j in range(4) if not np.any(A[drawn, j] != 0)]
+        Mo = orc.SampledM(smp)
+        Md = Mo.dense()
+        assert Mo.n_fixed_diag == len(missed) and 3 in missed
+        for j in range(4):
+            if j in missed:
+                assert Md[j, j] == 1.0
+                assert np.count_nonzero(Md[j]) == 1 and np.count_nonzero(Md[:, j]) == 1
+            else:
+                assert Md[j, j] > 0.0
+        seen_missed_2 |= 2 in missed
+        seen_hit_2 |= 2 not in missed
+    assert seen_missed_2 and seen_hit_2
 
 
 def test_sparse_and_dense_M_agree(orc):
@@ -294,6 +311,29 @@ def test_normal_matvec_matches_numpy(orc):
     p = np.random.default_rng(0).standard_normal(20)
     Ah = A / d
     np.testing.assert_allclose(orc.normal_matvec(mat, d, p), Ah.T @ (Ah @ p), rtol=1e-12)
+
+
+@pytest.mark.parametrize("normal_form", [False, True])
+def test_pcg_stop_test_is_relative(orc, normal_form):
+    """Alg. 2 step 4 stops on a relative residual, so the method is homogeneous in b:
+    scaling b (or h) by a power of two scales every iterate exactly and leaves the
+    iteration count, the restarts and the reported ratios unchanged, bit for bit."""
+    mat = W.udv_dense(400, 20, 1e3, 6)
+    smp = orc.Sample(mat, seed=4)
+    Mo = orc.SampledM(smp)
+    xs, b = W.rhs_for(mat, 1, 1e-3, 8)
+    v = orc.csr_rmatvec(mat, b[0]) / smp.d if normal_form else b[0]
+
+    def run(vec):
+        kw = {"h": vec} if normal_form else {"b": vec}
+        return orc.pcg(smp.mat, smp.d, Mo, tol=1e-10, maxit=1000, max_outer=5, **kw)
+    y0, i0 = run(v)
+    assert i0["converged"] == 1 and i0["iters"] > 5
+    for e in (-30, 30):
+        y, i = run(np.ldexp(v, e))
+        assert (i["iters"], i["outer"], i["converged"]) == (i0["iters"], i0["outer"], 1)
+        assert i["relres_true"] == i0["relres_true"] and i["relres_rec"] == i0["relres_rec"]
+        assert np.array_equal(y, np.ldexp(y0, e))
 
 
 @pytest.mark.parametrize("gen", ["gauss", "udv", "sparse", "semi"])

@@ -224,8 +224,13 @@ LSQ_API lsq_status lsq_precond_apply(const lsq_precond* P, const double* r, doub
  * pass over the rows of A, alpha = rho / ||Â p||^2, y += alpha p, g -= alpha w, stop when
  * ||g|| <= tol ||Â^T b||, z = P g, beta = rho'/rho, p = z + beta p.  On stop the true
  * residual Â^T (b - Â y) is recomputed (in FP64 from vals_f64 when given); if it misses
- * the tolerance PCG restarts from y (one outer step), up to o->max_outer times.  The whole
- * loop runs inside one persistent cooperative kernel.
+ * the tolerance PCG restarts from y (one outer step), up to o->max_outer times.
+ *
+ * Dense A (values F64, F32 or F32X2; BF16 returns LSQ_ERR_UNSUPPORTED): the whole loop of
+ * each column runs inside one persistent cooperative kernel.  CSR A (values F64, F32,
+ * BF16 or F32X2; P built with sweeps <= 32): each iteration is a row pass, a column pass
+ * and the level-ordered sweeps of Alg. 3; k >= 2 columns advance together in blocks of up
+ * to 32, with one pass over A and one sweep per iteration for the whole block.
  *
  *   A      matrix (device)
  *   P      handle built for this A

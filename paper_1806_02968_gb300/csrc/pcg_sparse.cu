@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
 }
 
 // The same sweep in ONE CTA, for deep and narrow level structures (few rows per level): the
-// levels follow one another at block barriers instead of completion counters.  Warp w takes
+// levels follow one another at block barriers instead of per-value waits.  Warp w takes
 // rows w, w + NW, ... of each level; the indices and values of its first row of the next level
 // (which do not depend on this sweep's values) are loaded before the barrier, so after it only
 // the gathers of e_new stand between two levels.
@@ -497,8 +497,9 @@ __global__ void k_gather_pairs(const float* src, const int64_t* perm, int64_t nn
 template <typename MT, bool FWD>
 static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* eold, double* enew,
                                int identity, int check, int nparts, int idx, cudaStream_t st) {
-    static int grid = 0;
+    static std::atomic<int> grid_cache{0};   // one per kernel instance; callers may be threads
     auto kern = k_sp_sweep_vf<MT, FWD>;
+    int grid = grid_cache.load(std::memory_order_relaxed);
     if (grid == 0) {
         int dev = 0, sms = 0, per = 0;
         LSQ_CUDA(cudaGetDevice(&dev));
@@ -506,6 +507,7 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
         LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SP_T, 0));
         if (per < 1) { set_error("sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
         grid = sms * per;
+        grid_cache.store(grid, std::memory_order_relaxed);
     }
     const int64_t nl = FWD ? a.one_f : a.one_b;
     if (nl > 0) {   // deep, narrow level structure: the whole sweep in one CTA
@@ -526,8 +528,8 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
 }
 
 // One CTA per sweep when a level holds fewer than 2048 dependency entries on average: block
-// barriers between levels are then cheaper than a grid of warps waiting on completion
-// counters, and one SM's loads still keep up with a level's gathers (at ~10,000 entries per
+// barriers between levels are then cheaper than a grid of warps polling for the values they
+// depend on, and one SM's loads still keep up with a level's gathers (at ~10,000 entries per
 // level one SM is twice slower than the grid).
 static void choose_sweep_form(SpArgs& a, const SparseHandle* SH, int64_t n) {
     const double dep = 0.5 * (double)(SH->nnz_M - n);   // dependency entries per direction

@@ -468,3 +468,39 @@ def test_adjoint_matches_closed_form_and_finite_differences(orc):
         E[i, j] = h
         fd = (loss(A + E, b)[0] - loss(A - E, b)[0]) / (2 * h)
         assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))
+
+
+# ---------------------------------------------------------------------------------------
+# Sec. 5.1-5.2: the iteration counts the paper prints for its well-conditioned examples.
+# The paper does not state b; a standard normal b is used.  CG on the normalised A is a
+# deterministic function of A, so its count must match the printed one up to the
+# realisation of A (+-1); RS must fall inside the printed mean +- (3 std + 1).  The
+# smaller rows keep the CPU suite short; all ten rows match (n up to 400).
+# ---------------------------------------------------------------------------------------
+def _paper_rows():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "paper_iterations.txt")):
+        if line.strip() and line[0] != "#":
+            f = line.split()
+            rows.append((f[0], int(f[1]), int(f[2]), int(f[3]), int(f[4]), float(f[5]), float(f[6])))
+    return rows
+
+
+@pytest.mark.parametrize("row", [r for r in _paper_rows() if r[1] <= 141],
+                         ids=lambda r: f"{r[0]}{r[1]}x{r[2]}")
+def test_iteration_counts_match_paper_tables(orc, row):
+    family, n, m, it_cg, it_rs, rs_mean, rs_std = row
+    mat = W.gaussian_dense(m, n, 1) if family == "gauss" else W.semi_gaussian_dense(m, n, 1)
+    b = np.random.default_rng(5).standard_normal(m)
+    counts = {}
+    for sweeps, seeds in ((0, [1]), (5, [1, 2, 3, 4])):
+        for sd in seeds:
+            smp = orc.Sample(mat, seed=sd)
+            assert smp.s == math.ceil(4 * n * math.log(n))
+            y, info = orc.pcg(smp.mat, smp.d, orc.SampledM(smp), b=b, tol=1e-7, maxit=1000,
+                              max_outer=5, sweeps=sweeps)
+            assert info["converged"] == 1 and info["relres_true"] <= 1e-7
+            counts.setdefault(sweeps, []).append(info["iters"])
+    assert abs(counts[0][0] - it_cg) <= 1, (counts, it_cg)
+    lo, hi = rs_mean - 3 * rs_std - 1, rs_mean + 3 * rs_std + 1
+    assert all(lo <= c <= hi for c in counts[5]), (counts[5], rs_mean, rs_std)

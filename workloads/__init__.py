@@ -58,20 +58,24 @@ def orthonormal_q(G: np.ndarray, matmul=None) -> np.ndarray:
     return Q
 
 
-def udv_dense(m: int, n: int, kappa: float, seed: int, matmul=None) -> dict:
+def udv_dense(m: int, n: int, kappa: float, seed: int, matmul=None, spacing: str = "log") -> dict:
     """A = U diag(sigma) V^T (Section 5.4, UDV matrix).
 
     U is the orthonormal Q factor of a seeded Gaussian m x n, V the Q factor of a
-    seeded Gaussian n x n (both with positive-diagonal R), and sigma is log-spaced from 1
-    down to 1/kappa, so that kappa(A) = kappa.  ``matmul`` may run the large products on
-    another device (see orthonormal_q).
+    seeded Gaussian n x n (both with positive-diagonal R).  sigma is log-spaced from 1
+    down to 1/kappa ("log"), or evenly spaced from 1 up to kappa ("linear", the paper's
+    D = diag[1, 1 + (c - 1)/n, ..., c] with c = kappa); either way kappa(A) = kappa.
+    ``matmul`` may run the large products on another device (see orthonormal_q).
     """
     rng = _rng(seed)
     G = rng.standard_normal((m, n))
     H = rng.standard_normal((n, n))
     U = orthonormal_q(G, matmul)
     V = orthonormal_q(H)
-    sigma = np.logspace(0.0, -math.log10(kappa), n)
+    if spacing == "linear":
+        sigma = np.linspace(1.0, kappa, n)
+    else:
+        sigma = np.logspace(0.0, -math.log10(kappa), n)
     mm = matmul or (lambda X, Y: X @ Y)
     A = np.asarray(mm(U * sigma[None, :], V.T))
     return {"kind": "dense", "A": np.ascontiguousarray(A), "sigma": sigma}

@@ -25,6 +25,18 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _require(cond, msg):
+    """Argument checks of the binding (kept under python -O, unlike assert)."""
+    if not cond:
+        raise ValueError(msg)
+
+
+def _device_array(t, name, dtype=None):
+    _require(isinstance(t, torch.Tensor) and t.is_cuda, f"{name} must be a CUDA tensor")
+    _require(dtype is None or t.dtype == dtype, f"{name} must be {dtype}")
+    _require(t.is_contiguous(), f"{name} must be contiguous")
+
+
 def opts(**kw) -> L.LsqOpts:
     """lsq_default_opts() with keyword overrides."""
     o = L.LsqOpts()
@@ -42,9 +54,11 @@ class Matrix:
     def __init__(self, dense=None, *, row_ptr=None, col_idx=None, vals=None, n=None,
                  vals_f64=None, f32x2=None):
         if dense is not None:
-            assert dense.is_cuda and dense.dim() == 2 and dense.stride(1) == 1
+            _require(isinstance(dense, torch.Tensor) and dense.is_cuda, "A must be a CUDA tensor")
+            _require(dense.dim() == 2 and dense.stride(1) == 1, "dense A must be 2-D with unit column stride")
             if f32x2:   # (m, 2 n) float32: element j of row i is the pair at columns 2j, 2j+1
-                assert dense.dtype == torch.float32 and dense.shape[1] % 2 == 0
+                _require(dense.dtype == torch.float32 and dense.shape[1] % 2 == 0,
+                         "double-float A must be float32 (m, 2 n) pairs")
                 self.m, self.n = dense.shape[0], dense.shape[1] // 2
                 self.ld = dense.stride(0) // 2
             else:
@@ -55,13 +69,19 @@ class Matrix:
             self.nnz = self.m * self.n
             self.dense = True
         else:
-            assert row_ptr.dtype == torch.int64 and col_idx.dtype == torch.int32
+            _device_array(row_ptr, "row_ptr", torch.int64)
+            _device_array(col_idx, "col_idx", torch.int32)
+            _device_array(vals, "vals")
+            _require(n is not None and int(n) > 0, "CSR A needs its column count n")
             self.m = row_ptr.numel() - 1
             self.n = int(n)
             self.ld = 0
             self.vals, self.row_ptr, self.col_idx = vals, row_ptr, col_idx
             self.nnz = vals.numel()
             self.dense = False
+        _require(f32x2 or self.vals.dtype in DTYPES, "values must be float64, float32 or bfloat16")
+        if vals_f64 is not None:
+            _require(vals_f64.is_cuda and vals_f64.dtype == torch.float64, "vals_f64 must be a CUDA float64 tensor")
         self.dtype = L.LSQ_F32X2 if f32x2 else DTYPES[self.vals.dtype]
         self.vals_f64 = vals_f64
         self.c = L.LsqMatrix(self.m, self.n, self.nnz, 1 if self.dense else 0, self.ld,
@@ -197,10 +217,13 @@ def lsq_pcg_solve(A: Matrix, P: Precond, B, o=None, X=None, stream=None, raise_o
     """Alg. 2 step 4 for k right-hand sides (B: (m,) or (k, m) float64) -> (X, Info)."""
     o = o or opts()
     B2 = B.reshape(1, -1) if B.dim() == 1 else B
-    assert B2.dtype == torch.float64 and B2.stride(1) == 1
+    _require(B2.is_cuda and B2.dtype == torch.float64 and B2.stride(1) == 1,
+             "B must be a CUDA float64 tensor (m,) or (k, m) with unit stride along m")
     k = B2.shape[0]
     if X is None:
         X = torch.empty(k, A.n, dtype=torch.float64, device=B.device)
+    _require(X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.shape[0] == k
+             and X.shape[1] >= A.n and X.stride(1) == 1, "X must be a CUDA float64 (k, n) tensor")
     ci, arrs = _info(k)
     code = L.load().lsq_pcg_solve(A.ref, P.h, _ptr(B2), k, B2.stride(0), _ptr(X), X.stride(0),
                                   C.byref(o), C.byref(ci), _stream(stream))
@@ -266,8 +289,10 @@ class Batch:
         arr = (L.LsqBatchProblem * len(problems))()
         for i, (A, n, P, B) in enumerate(problems):
             B2 = B.reshape(1, -1) if B.dim() == 1 else B
-            assert A.dtype == torch.float32 and A.is_cuda and A.stride(1) == 1
-            assert B2.dtype == torch.float64 and B2.stride(1) == 1 and B2.shape[0] == self.k
+            _require(A.is_cuda and A.dtype == torch.float32 and A.stride(1) == 1,
+                     "each batch A must be a CUDA float32 row-major tensor")
+            _require(B2.is_cuda and B2.dtype == torch.float64 and B2.stride(1) == 1 and B2.shape[0] == self.k,
+                     "each batch B must be a CUDA float64 (k, m) tensor with the batch's k")
             X = torch.zeros(self.k, n, dtype=torch.float64, device=A.device)
             self.keep += [A, B2, P]
             self.X.append(X)

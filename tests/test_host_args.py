@@ -165,3 +165,19 @@ def test_split_f64_checks_and_empty_input(lsq):
     assert L.lsq_split_f64(None, FAKE, 4, None) == 1
     assert L.lsq_split_f64(FAKE, FAKE, -1, None) == 1
     assert L.lsq_split_f64(FAKE, FAKE, 0, None) == 0     # nothing to convert: no launch
+
+
+def test_binding_rejects_host_tensors_before_calling_the_library(lsq):
+    """The Python layer checks where its tensors live before it hands pointers over (the C
+    library cannot tell a host pointer from a device one)."""
+    import types
+    import torch
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        lsq.Matrix(torch.zeros(8, 3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="row_ptr must be a CUDA tensor"):
+        lsq.Matrix(row_ptr=torch.zeros(4, dtype=torch.int64), col_idx=torch.zeros(2, dtype=torch.int32),
+                   vals=torch.zeros(2, dtype=torch.float64), n=2)
+    with pytest.raises(ValueError, match="B must be a CUDA float64"):
+        lsq.lsq_pcg_solve(types.SimpleNamespace(n=3), None, torch.zeros(8, dtype=torch.float64))
+    with pytest.raises(KeyError):
+        lsq.opts(no_such_option=1)

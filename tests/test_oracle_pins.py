@@ -209,6 +209,28 @@ def test_sampled_normal_matrix_is_unbiased(orc):
     assert np.all(np.abs(mean - N) <= 5 * se + 1e-12)
 
 
+def test_spectral_error_within_the_paper_bound(orc):
+    """Sec. 3.2, the approximation theorem: for ||Â||_F^2 = n, eps and delta in (0, 1),
+    C = (2/3)(6 ||Â||^2 + 2 eps)(1 - log_n(delta / 2)) and s = C eps^-2 n log n give
+    ||A_s^T A_s - Â^T Â||_2 <= eps with probability at least 1 - delta.  Twenty seeds must
+    all meet it, and the error must shrink like s^(-1/2) (the matrix Bernstein rate)."""
+    mat = W.gaussian_dense(2000, 20, 3)
+    n = 20
+    Ah = mat["A"] / np.linalg.norm(mat["A"], axis=0)
+    N = Ah.T @ Ah
+    eps, delta = 0.5, 0.01
+    C = (2.0 / 3.0) * (6.0 * np.linalg.norm(Ah, 2) ** 2 + 2.0 * eps) * (1.0 - math.log(delta / 2) / math.log(n))
+    s = math.ceil(C * n * math.log(n) / eps ** 2)
+
+    def err(seed, draws):
+        return np.linalg.norm(orc.SampledM(orc.Sample(mat, seed=seed, s=draws)).dense() - N, 2)
+    errs = [err(sd, s) for sd in range(20)]
+    assert max(errs) <= eps, (s, max(errs))
+    errs16 = [err(sd, 16 * s) for sd in range(5)]
+    ratio = np.mean(errs16) / np.mean(errs[:5])
+    assert 0.15 <= ratio <= 0.4, ratio           # 1/sqrt(16) = 0.25
+
+
 def test_unsampled_column_gets_unit_diagonal(orc):
     """A column no drawn row touches has M_jj = 0; it becomes 1, the diagonal of the
     normalised A^T A, and it is the only entry of its row and column.  Column 2 lives in

@@ -196,18 +196,19 @@ LSQ_API lsq_status lsq_build_precond(const lsq_matrix* A, const int32_t* idx, co
  * the handle was built on. */
 LSQ_API void lsq_precond_destroy(lsq_precond* P);
 
-/* Copy the assembled M = A_s^T A_s out of a handle (dense: row-major n x n into M_out,
- * device double[n*n]).  For checking and diagnostics. */
+/* Copy the assembled M = A_s^T A_s of Sec. 3.3 out of a dense handle (row-major n x n into
+ * M_out, device double[n*n]).  For checking and diagnostics.  LSQ_ERR_INVALID for a NULL
+ * argument or a sparse handle. */
 LSQ_API lsq_status lsq_precond_get_M(const lsq_precond* P, double* M_out, void* stream);
 
-/* Sparse handles: number of stored entries of M = A_s^T A_s in *nnz_out, and (when the
- * pointers are not NULL) M in CSR with sorted columns and the diagonal always stored:
- * row_ptr device int64[n+1], col_idx device int32[nnz], vals device double[nnz]. */
+/* Sparse handles: number of stored entries of M = A_s^T A_s (Sec. 3.3) in *nnz_out, and
+ * (when the pointers are not NULL) M in CSR with sorted columns and the diagonal always
+ * stored: row_ptr device int64[n+1], col_idx device int32[nnz], vals device double[nnz]. */
 LSQ_API lsq_status lsq_precond_get_M_csr(const lsq_precond* P, int64_t* nnz_out, int64_t* row_ptr,
                                          int32_t* col_idx, double* vals, void* stream);
 
-/* Copy the materialised SGS operator (dense handles only, row-major n x n, device
- * double[n*n], converted to FP64). */
+/* Copy the materialised SGS operator P of Alg. 3 (dense handles only, row-major n x n,
+ * device double[n*n], converted to FP64): column j is Alg. 3 applied to the unit vector e_j. */
 LSQ_API lsq_status lsq_precond_get_op(const lsq_precond* P, double* op_out, void* stream);
 
 /* Apply the preconditioner of Alg. 3: e = P r for k vectors (device, column c at
@@ -315,7 +316,8 @@ LSQ_API lsq_status lsq_batch_info(const lsq_batch* b, lsq_info* infos, void* str
 LSQ_API void lsq_batch_destroy(lsq_batch* b);
 
 /* Convert FP64 values to the LSQ_F32X2 pair format (hi = RN(v), lo = RN(v - hi)),
- * count elements, device to device. */
+ * count elements, device to device (a storage form of this library, not in the paper).
+ * LSQ_ERR_INVALID for NULL pointers or count < 0; count = 0 launches nothing. */
 LSQ_API lsq_status lsq_split_f64(const double* src, float* dst_pairs, int64_t count, void* stream);
 
 /* Human-readable name of a status code. */

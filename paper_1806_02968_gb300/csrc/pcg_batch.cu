@@ -338,12 +338,6 @@ struct BtState {
 };
 static_assert(sizeof(BtState) <= 32 * 32 * 8, "state does not fit its shared-memory slot");
 
-__device__ __forceinline__ unsigned bt_cluster_id() {
-    unsigned v;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(v));
-    return v;
-}
-
 // Per-column totals over the cluster of the two partial vectors in slot `sl`, read through
 // distributed shared memory in rank order: t0[c], t1[c] (c < KC), then a block barrier.
 template <int KC>

@@ -173,15 +173,6 @@ __global__ void __launch_bounds__(SP_T) k_sp_update(SpArgs a, int nparts) {
     if (threadIdx.x == 0) a.part[a.rblk + blockIdx.x] = t;
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // One Gauss-Seidel sweep of Alg. 3 on M (FWD: rows in natural order, lower entries are
 // the dependencies; otherwise reverse order, upper entries):
 //   e_new_j = (r_j - sum_{other side} M_jk e_old_k - sum_{dependency side} M_jk e_new_k) / M_jj

@@ -75,15 +75,6 @@ struct BkArgs {
     int32_t maxit;
 };
 
-__device__ __forceinline__ unsigned long long bk_ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void bk_red_release_add_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // Thread t holds v for column t % GK; out[c] = that column's sum over the block (fixed order).
 __device__ __forceinline__ void bk_block_partials(double v, int K, int GK, double* out, double* sh) {
     sh[threadIdx.x] = v;

@@ -1,0 +1,41 @@
+"""bench.py's reference arm (the oracle on the host cores) prints the contract's JSON line,
+and only rank 0 prints it.  A tiny UDV case keeps this a CPU test of seconds."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ARGS = ["--impl", "reference", "--m", "4096", "--n", "64", "--kappa", "1e3", "--steps", "2",
+        "--warmup", "0", "--cpu-iters", "2"]
+
+
+def _run(env_extra):
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *ARGS], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = _run({"LSQ_REF_ITERS": "500"})
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in rec, key
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 1 and rec["steps"] == 2
+    assert rec["higher_is_better"] is True and rec["unit"] == "solves/s" and rec["vs_baseline"] is None
+    assert rec["config"]["workload"] == "udv_dense_4096x64_kappa1000"
+    assert rec["value"] > 0 and abs(rec["value"] * rec["ms_per_step"] / 1e3 - 1.0) < 1e-9
+    cb = rec["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == rec["value"] and "500" in cb["sample"]
+    e2e = rec["e2e"]
+    assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    out = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert out.returncode == 0 and not out.stdout.strip()

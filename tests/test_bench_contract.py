@@ -39,3 +39,22 @@ def test_reference_arm_prints_the_contract_line():
 def test_reference_arm_runs_on_rank_zero_only():
     out = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out.returncode == 0 and not out.stdout.strip()
+
+
+def test_roofline_bytes_of_the_benchmark_launch():
+    """The algorithmic bytes bench.py divides by the kernel time: per PCG iteration one pass
+    over A (m n elem) and one over the n x n SGS operator, plus the FP64 residual passes.
+    At 262144 x 512 in double-float pairs that is 1,075,838,976 B per iteration, which at
+    the measured 278.6 us per iteration is the 3.86 TB/s quoted for the benchmark."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    m, n, it = 262144, 512, 110802
+    info = types.SimpleNamespace(iters=[it], outer=[1])
+    byts, flops = bench.pcg_algorithmic(None, m, n, info, 8, 8, 8)
+    per_iter = m * n * 8 + n * n * 8
+    assert per_iter == 1_075_838_976
+    residual = 2 * (m * n * 8 + 8 * m)             # h = Â^T b and the final true residual
+    assert byts == it * per_iter + residual
+    assert abs(per_iter / 278.6e-6 / 1e12 - 3.86) < 0.005
+    assert flops == it * (4.0 * m * n + 2.0 * n * n) + 2 * 4.0 * m * n

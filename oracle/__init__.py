@@ -1,7 +1,7 @@
 """Python face of the FP64 CPU oracle (``oracle/lsq_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()`` and by
-the benchmark's CPU-baseline leg, never by the CUDA package.  It shares no code with
+the benchmark's CPU legs (the CPU baseline and the reference arm), never by the CUDA package.  It shares no code with
 the CUDA path.  Matrices use the dict layout of :mod:`workloads`.
 
 Each wrapper names the step of the paper it computes (Alg. 1-3, Eq. R2P, Sec. 3.3).

@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct statement
  * of what the CUDA path computes.  Only the test suite, the smoke check and the
- * benchmark's CPU-baseline leg may load it.  It shares no code, header or constant
+ * benchmark's CPU legs (the CPU baseline and the reference arm) may load it.  It shares no code, header or constant
  * table with the CUDA library, and the CUDA library never calls it.
  *
  * Every function follows one step of the paper, in the paper's order and notation:

@@ -4,7 +4,8 @@ import pytest
 import torch
 
 import workloads as W
-from helpers import rel, to_device
+from helpers import (assert_iterations, assert_solution, record_parity, rel, rounding_variant_iters,
+                     to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -66,8 +67,8 @@ def test_sgs_operator_ill_conditioned_and_f32(lsq, orc):
     assert rel(e32, ref) <= 1e-4
 
 
-def _solve_and_compare(lsq, orc, mat, seed, noise, tol=1e-10, iter_slack=2, dtype="f64",
-                       with_f64=False, pdt=0, k=1, **okw):
+def _solve_and_compare(lsq, orc, mat, seed, noise, tol=1e-10, check_iters=True, dtype="f64",
+                       with_f64=False, pdt=0, k=1, what="", **okw):
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, seed, dtype=dtype, pdt=pdt, with_f64=with_f64)
     for kk, v in okw.items():
         setattr(o, kk, v)
@@ -86,39 +87,87 @@ def _solve_and_compare(lsq, orc, mat, seed, noise, tol=1e-10, iter_slack=2, dtyp
         r = A.T @ (b[c] - A @ X[c])
         raw = np.linalg.norm(r) / np.linalg.norm(A.T @ b[c])
         assert abs(raw - info.relres_raw[c]) <= 1e-3 * raw + 1e-15
-        # both solutions satisfy the normal equation to tol: they can differ by
-        # kappa(Â)^2 (tol_gpu + tol_oracle) in the worst direction, and no more
-        assert rel(X[c], x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * tol)
-        if iter_slack is not None:
-            assert abs(int(info.iters[c]) - oi["iters"]) <= iter_slack, (info.iters[c], oi["iters"])
+        assert_solution(X[c], x_or, kappa, f"{what} column {c}")
+        if check_iters:
+            assert_iterations(info.iters[c], oi["iters"],
+                              lambda: rounding_variant_iters(orc, seen, smp, Mo, b[c], tol, o.sweeps,
+                                                             o.maxit, o.max_outer),
+                              f"{what} column {c}")
     return info
 
 
 def test_pcg_config1_gaussian(lsq, orc):
     # 4096 x 128 Gaussian, b = A x* + 1e-3 noise, one forward + one backward sweep, 1e-10
-    info = _solve_and_compare(lsq, orc, W.gaussian_dense(4096, 128, 1001), 1001, 1e-3)
+    info = _solve_and_compare(lsq, orc, W.gaussian_dense(4096, 128, 1001), 1001, 1e-3, what="gauss4096x128")
     assert info.iters[0] < 40
 
 
 @pytest.mark.parametrize("shape", [(3001, 70), (20000, 256), (9000, 1000)])
 def test_pcg_ragged_and_large_n(lsq, orc, shape):
     m, n = shape
-    _solve_and_compare(lsq, orc, W.gaussian_dense(m, n, 11), 11, 1e-2)
+    _solve_and_compare(lsq, orc, W.gaussian_dense(m, n, 11), 11, 1e-2, what=f"gauss{m}x{n}")
 
 
 def test_pcg_udv_moderate_condition(lsq, orc):
-    _solve_and_compare(lsq, orc, W.udv_dense(16384, 64, 1e3, 2), 1002, 1e-6, iter_slack=None)
+    _solve_and_compare(lsq, orc, W.udv_dense(16384, 64, 1e3, 2), 1002, 1e-6, what="udv16384x64 kappa 1e3")
+
+
+@pytest.mark.parametrize("tol", [1e-13])
+def test_pcg_tight_tolerance_kappa_1e3(lsq, orc, tol):
+    """At tol = 1e-13 even the worst-case gap of two solutions meeting the tolerance,
+    4 kappa^2 tol, is below the solution bar 1e-8 kappa at kappa(Â) = 1e3."""
+    _solve_and_compare(lsq, orc, W.udv_dense(16384, 64, 1e3, 2), 1002, 1e-6, tol=tol,
+                       what="udv16384x64 kappa 1e3 tol 1e-13")
+
+
+@pytest.mark.parametrize("form", ["f64", "f32x2"])
+def test_pcg_headline_conditioning_kappa_1e6(lsq, orc, form):
+    """The benchmark's conditioning, kappa(A) = 1e6 (kappa(Â^T Â) ~ 1e12), at a size the
+    oracle finishes: FP64 values, and double-float values with FP64 restarts (the benchmark's
+    form).  tol = 1e-13, where the solution is determined to well inside the bar
+    1e-8 kappa(Â) = 1e-2 (at 1e-10 the residual leaves the components along the smallest
+    singular directions free: the oracle lands 0.94 from LAPACK there, 1.8e-4 at 1e-13)."""
+    mat = W.udv_dense(16384, 64, 1e6, 2)
+    seed, tol = 1002, 1e-13
+    A64 = torch.from_numpy(mat["A"]).cuda()
+    Mx64 = lsq.Matrix(A64)
+    o = lsq.opts(seed=seed, tol=tol, max_outer=40)
+    idx, p, d = lsq.lsq_sample_rows(Mx64, o)
+    P = lsq.lsq_build_precond(Mx64, idx, p, d, o)
+    Mx = Mx64 if form == "f64" else lsq.Matrix(lsq.lsq_split_f64(A64), f32x2=True, vals_f64=A64)
+    xs, b = W.rhs_for(mat, 1, 1e-6, seed + 7)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
+    smp = orc.Sample(mat, seed=seed)
+    assert np.array_equal(idx.cpu().numpy(), smp.idx)
+    Mo = orc.SampledM(smp)
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=tol, maxit=o.maxit, max_outer=o.max_outer)
+    assert oi["converged"] == 1 and info.converged[0] == 1 and info.relres_true[0] <= tol
+    kappa = np.linalg.cond(mat["A"] / smp.d)
+    assert kappa > 5e5
+    x = X.cpu().numpy()
+    assert_solution(x, y / smp.d, kappa, f"udv16384x64 kappa 1e6 {form}")
+    # the reported true residual, recomputed here in FP64 from A itself
+    Ah = mat["A"] / smp.d
+    g = Ah.T @ (b[0] - mat["A"] @ x)
+    assert np.linalg.norm(g) / np.linalg.norm(Ah.T @ b[0]) <= 2 * tol
+    if form == "f64":
+        assert_iterations(info.iters[0], oi["iters"],
+                          lambda: rounding_variant_iters(orc, mat, smp, Mo, b[0], tol, 1, o.maxit, o.max_outer),
+                          "udv16384x64 kappa 1e6 f64")
+    else:   # other arithmetic (about 48 bits) in the inner iteration: recorded, not held to +-2
+        record_parity("udv16384x64 kappa 1e6 double-float", gpu_iters=int(info.iters[0]),
+                      oracle_iters=int(oi["iters"]), outer=int(info.outer[0]))
 
 
 def test_pcg_multiple_rhs_and_sweeps(lsq, orc):
-    _solve_and_compare(lsq, orc, W.gaussian_dense(5000, 100, 4), 4, 1e-3, k=3, sweeps=1)
+    _solve_and_compare(lsq, orc, W.gaussian_dense(5000, 100, 4), 4, 1e-3, k=3, what="gauss5000x100 k3")
 
 
 def test_pcg_f32_values_with_f64_refinement(lsq, orc):
     # precision form: FP32 A and operator in the iteration, FP64 residuals/dots/updates
     info = _solve_and_compare(lsq, orc, W.udv_dense(16384, 128, 1e2, 3), 1002, 1e-6,
-                              dtype="f32", with_f64=True, pdt=1, iter_slack=None, max_outer=30,
-                              inner_tol=1e-4)
+                              dtype="f32", with_f64=True, pdt=1, check_iters=False, max_outer=30,
+                              inner_tol=1e-4, what="udv16384x128 FP32 values")
     assert info.outer[0] >= 1
 
 
@@ -202,13 +251,16 @@ def test_pcg_double_float_storage(lsq, orc, with_f64):
     x_or = y / smp.d
     kappa = np.linalg.cond(mat["A"] / smp.d)
     assert info.converged[0] == 1 and info.relres_true[0] <= o.tol
-    assert rel(X.cpu().numpy(), x_or) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
-    # At kappa(Â^T Â) = 1e6 the CG iteration count depends on rounding: measured, the FP64
-    # GPU path (same arithmetic as the oracle, another summation order in the fused pass and
-    # the reductions) lands 8% from the oracle's count, and double-float products (unit
-    # roundoff 2^-48) land closer than that.  Both are held to 12%.
-    assert abs(int(info64.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info64.iters[0], oi["iters"])
-    assert abs(int(info.iters[0]) - oi["iters"]) <= max(2, 0.12 * oi["iters"]), (info.iters[0], oi["iters"])
+    assert_solution(X.cpu().numpy(), x_or, kappa, "udv16384x128 double-float")
+    assert_solution(X64.cpu().numpy(), x_or, kappa, "udv16384x128 FP64")
+    # kappa(Â^T Â) ~ 1e6: CG's count moves with rounding (tests/test_oracle_rounding.py)
+    variants = []
+    def var():
+        if not variants:
+            variants.extend(rounding_variant_iters(orc, mat, smp, Mo, b[0], o.tol, 1, o.maxit, o.max_outer))
+        return variants
+    assert_iterations(info64.iters[0], oi["iters"], var, "udv16384x128 kappa 1e3 FP64")
+    assert_iterations(info.iters[0], oi["iters"], var, f"udv16384x128 kappa 1e3 double-float f64={with_f64}")
 
 
 @pytest.mark.parametrize("gen", ["gauss", "udv"])
@@ -224,7 +276,7 @@ def test_cg_baseline_dense_matches_oracle(lsq, orc, gen):
     for c in range(2):
         y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=0)
         assert info.converged[c] == 1 and oi["converged"] == 1
-        assert rel(X[c], y / smp.d) <= max(1e-8 * kappa, 4 * kappa ** 2 * o.tol)
-        # without the SGS preconditioner the counts at kappa(Â^T Â) = 1e4 move with the
-        # summation order (193 vs 204 measured): the 12% band of ill-conditioned cases
-        assert abs(int(info.iters[c]) - oi["iters"]) <= max(2, 0.12 * oi["iters"])
+        assert_solution(X[c], y / smp.d, kappa, f"CG {gen} column {c}")
+        assert_iterations(info.iters[c], oi["iters"],
+                          lambda: rounding_variant_iters(orc, seen, smp, Mo, b[c], o.tol, 0, o.maxit, o.max_outer),
+                          f"CG {gen} column {c}")

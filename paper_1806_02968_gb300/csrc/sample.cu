@@ -11,6 +11,7 @@
 namespace lsq {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<uint32_t> g_wait_polls{0};
 static thread_local std::string t_err;
 void set_error(const std::string& msg) { t_err = msg; }
 const char* last_error() { return t_err.c_str(); }
@@ -354,34 +355,51 @@ static int grid_for(int64_t work, int threads, int cap = 152 * 16) {
     return (int)g;
 }
 
-template <int DT>
-static lsq_status sample_impl(const lsq_matrix* A, const lsq_opts* o, int64_t s,
-                              int32_t* idx_out, double* p_out, double* colscale_out,
-                              cudaStream_t st) {
-    const int64_t m = A->m, n = A->n;
-    // scratch layout (256-byte aligned pieces); the first three are zero-initialised
+// Scratch layout of one sampling call (256-byte aligned pieces; the first three are the
+// accumulating words that must start at zero).
+struct SampleLayout {
+    size_t err, amax, c, E1g, E1j, d2, inv, d, w, P, ts, total;
+};
+constexpr size_t rnd256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr SampleLayout sample_layout(int64_t m, int64_t n) {
+    SampleLayout L{};
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
-    size_t o_err = take(16), o_amax = take(8 * n), o_c = take(16 * n), o_E1g = take(16),
-           o_E1j = take(4 * n), o_d2 = take(8 * n), o_inv = take(8 * n), o_d = take(8 * n),
-           o_w = take(16 * m), o_P = take(16 * (m + 1));
-    int64_t ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
-    size_t o_ts = take(16 * ntiles);
-    Scratch sc;
-    LSQ_CUDA(sc.alloc(off, st));
-    char* base = sc.as<char>();
-    unsigned* err = (unsigned*)(base + o_err);
-    unsigned long long* amax = (unsigned long long*)(base + o_amax);
-    u128* c = (u128*)(base + o_c);
-    unsigned* E1g = (unsigned*)(base + o_E1g);
-    int* E1j = (int*)(base + o_E1j);
-    double* d2 = (double*)(base + o_d2);
-    double* inv = (double*)(base + o_inv);
-    double* d = colscale_out ? colscale_out : (double*)(base + o_d);
-    u128* w = (u128*)(base + o_w);
-    u128* P = (u128*)(base + o_P);
-    u128* ts = (u128*)(base + o_ts);
-    LSQ_CUDA(cudaMemsetAsync(base, 0, o_E1g, st));
+    L.err = off;  off += rnd256(16);
+    L.amax = off; off += rnd256(8 * n);
+    L.c = off;    off += rnd256(16 * n);
+    L.E1g = off;  off += rnd256(16);
+    L.E1j = off;  off += rnd256(4 * n);
+    L.d2 = off;   off += rnd256(8 * n);
+    L.inv = off;  off += rnd256(8 * n);
+    L.d = off;    off += rnd256(8 * n);
+    L.w = off;    off += rnd256(16 * m);
+    L.P = off;    off += rnd256(16 * (m + 1));
+    L.ts = off;   off += rnd256(16 * ((m + SCAN_TILE - 1) / SCAN_TILE));
+    L.total = off;
+    return L;
+}
+
+// S1-S4 on the scratch at `base` (laid out by sample_layout): the nine kernels of one
+// sampling call, then the device error word.  Every word that accumulates is cleared
+// first, so the scratch may hold anything on entry.
+template <int DT>
+static lsq_status sample_launch(const lsq_matrix* A, const lsq_opts* o, int64_t s, int32_t* idx_out,
+                                double* p_out, double* colscale_out, char* base, cudaStream_t st) {
+    const int64_t m = A->m, n = A->n;
+    const SampleLayout L = sample_layout(m, n);
+    const int64_t ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+    unsigned* err = (unsigned*)(base + L.err);
+    unsigned long long* amax = (unsigned long long*)(base + L.amax);
+    u128* c = (u128*)(base + L.c);
+    unsigned* E1g = (unsigned*)(base + L.E1g);
+    int* E1j = (int*)(base + L.E1j);
+    double* d2 = (double*)(base + L.d2);
+    double* inv = (double*)(base + L.inv);
+    double* d = colscale_out ? colscale_out : (double*)(base + L.d);
+    u128* w = (u128*)(base + L.w);
+    u128* P = (u128*)(base + L.P);
+    u128* ts = (u128*)(base + L.ts);
+    LSQ_CUDA(cudaMemsetAsync(base, 0, L.E1g, st));
     LSQ_CUDA(cudaMemsetAsync(E1g, 0xff, 16, st));
 
     lsq_matrix Av = *A;
@@ -389,50 +407,44 @@ static lsq_status sample_impl(const lsq_matrix* A, const lsq_opts* o, int64_t s,
     if (A->dense) {
         rpb = (m + 152 * 8 - 1) / (152 * 8);
         if (rpb < 16) rpb = 16;
-        int g = (int)((m + rpb - 1) / rpb);
-        k_colmax_dense<DT><<<g, 256, 0, st>>>(Av, amax, err, rpb);
+        k_colmax_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, amax, err, rpb);
     } else {
         k_colmax_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, amax, err);
     }
     k_col_exponents<<<grid_for(n, 256), 256, 0, st>>>(n, amax, E1j, E1g, err);
-    count_launch(2);
-    if (A->dense) {
-        int g = (int)((m + rpb - 1) / rpb);
-        k_colsum_dense<DT><<<g, 256, 0, st>>>(Av, E1j, c, rpb);
-    } else {
-        k_colsum_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, E1j, c);
-    }
-    count_launch();
+    if (A->dense) k_colsum_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, E1j, c, rpb);
+    else k_colsum_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, E1j, c);
     k_colscale<<<grid_for(n, 256), 256, 0, st>>>(n, o->normalize ? 1 : 0, E1j, E1g, c, d2, inv, d);
-    count_launch();
     k_rowweight<DT><<<grid_for(m * 32, 256), 256, 0, st>>>(Av, inv, w);
-    count_launch();
     k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts);
     k_scan_sums<<<1, 1024, 0, st>>>(ts, ntiles);
     k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts, P);
-    count_launch(3);
     k_draw<<<grid_for(s, 256), 256, 0, st>>>(P, m, s, (unsigned long long)o->seed, idx_out, p_out, err);
-    count_launch();
+    count_launch(9);
     LSQ_CUDA(cudaGetLastError());
     return read_dev_error(err, st);
 }
 
+template <int DT>
+static lsq_status sample_impl(const lsq_matrix* A, const lsq_opts* o, int64_t s,
+                              int32_t* idx_out, double* p_out, double* colscale_out,
+                              cudaStream_t st) {
+    Scratch sc;
+    LSQ_CUDA(sc.alloc(sample_layout(A->m, A->n).total, st));
+    return sample_launch<DT>(A, o, s, idx_out, p_out, colscale_out, sc.as<char>(), st);
+}
+
 // ---------------------------------------------------------------------------------------
-// Fixed scratch for lsq_sample_rows_static: the same kernels as lsq_sample_rows, with the
+// Fixed scratch for lsq_sample_rows_static: the same launcher as lsq_sample_rows, with the
 // scratch carved from one file-scope device array instead of a stream-ordered allocation.
 // ---------------------------------------------------------------------------------------
 constexpr int64_t STATIC_MAX_ROWS = 262144;
 constexpr int64_t STATIC_MAX_COLS = 4096;
-constexpr size_t rnd256(size_t b) { return (b + 255) & ~size_t(255); }
-// byte size of the scratch layout used below, for m rows and n columns
-constexpr size_t static_scratch_bytes(int64_t m, int64_t n) {
-    return rnd256(16) + rnd256(8 * n) + rnd256(16 * n) + rnd256(16) + rnd256(4 * n) + 3 * rnd256(8 * n) +
-           rnd256(16 * m) + rnd256(16 * (m + 1)) + rnd256(16 * ((m + SCAN_TILE - 1) / SCAN_TILE));
-}
-constexpr size_t STATIC_SCRATCH_BYTES = static_scratch_bytes(STATIC_MAX_ROWS, STATIC_MAX_COLS);
+constexpr size_t STATIC_SCRATCH_BYTES = sample_layout(STATIC_MAX_ROWS, STATIC_MAX_COLS).total;
 static __device__ __align__(256) unsigned char g_sample_scratch[STATIC_SCRATCH_BYTES];
 
-// Device address of g_sample_scratch on the current device, looked up once per device.
+// Device address of g_sample_scratch on the current device, looked up once per device and
+// kept for the life of the process's primary context on that device.
 static lsq_status static_scratch_address(char** out) {
     static std::mutex mu;
     static void* addr[64] = {};
@@ -452,50 +464,11 @@ static lsq_status static_scratch_address(char** out) {
 template <int DT>
 static lsq_status sample_into_static(const lsq_matrix* A, const lsq_opts* o, int64_t s, int32_t* idx_out,
                                      double* p_out, double* colscale_out, char* base, cudaStream_t st) {
-    const int64_t m = A->m, n = A->n;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t at = off; off += rnd256(bytes); return at; };
-    size_t o_err = take(16), o_amax = take(8 * n), o_c = take(16 * n), o_E1g = take(16),
-           o_E1j = take(4 * n), o_d2 = take(8 * n), o_inv = take(8 * n), o_d = take(8 * n),
-           o_w = take(16 * m), o_P = take(16 * (m + 1));
-    const int64_t ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
-    size_t o_ts = take(16 * ntiles);
-    if (off > STATIC_SCRATCH_BYTES) { set_error("static scratch layout exceeds its array"); return LSQ_ERR_INVALID; }
-    unsigned* err = (unsigned*)(base + o_err);
-    unsigned long long* amax = (unsigned long long*)(base + o_amax);
-    u128* c = (u128*)(base + o_c);
-    unsigned* E1g = (unsigned*)(base + o_E1g);
-    int* E1j = (int*)(base + o_E1j);
-    double* d2 = (double*)(base + o_d2);
-    double* inv = (double*)(base + o_inv);
-    double* d = colscale_out ? colscale_out : (double*)(base + o_d);
-    u128* w = (u128*)(base + o_w);
-    u128* P = (u128*)(base + o_P);
-    u128* ts = (u128*)(base + o_ts);
-    // the array keeps the previous call's contents: clear everything that accumulates
-    LSQ_CUDA(cudaMemsetAsync(base, 0, o_E1g, st));
-    LSQ_CUDA(cudaMemsetAsync(E1g, 0xff, 16, st));
-    lsq_matrix Av = *A;
-    int64_t rpb = 0;
-    if (A->dense) {
-        rpb = (m + 152 * 8 - 1) / (152 * 8);
-        if (rpb < 16) rpb = 16;
-        k_colmax_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, amax, err, rpb);
-    } else {
-        k_colmax_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, amax, err);
+    if (sample_layout(A->m, A->n).total > STATIC_SCRATCH_BYTES) {
+        set_error("static scratch layout exceeds its array");
+        return LSQ_ERR_INVALID;
     }
-    k_col_exponents<<<grid_for(n, 256), 256, 0, st>>>(n, amax, E1j, E1g, err);
-    if (A->dense) k_colsum_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, E1j, c, rpb);
-    else k_colsum_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, E1j, c);
-    k_colscale<<<grid_for(n, 256), 256, 0, st>>>(n, o->normalize ? 1 : 0, E1j, E1g, c, d2, inv, d);
-    k_rowweight<DT><<<grid_for(m * 32, 256), 256, 0, st>>>(Av, inv, w);
-    k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts);
-    k_scan_sums<<<1, 1024, 0, st>>>(ts, ntiles);
-    k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts, P);
-    k_draw<<<grid_for(s, 256), 256, 0, st>>>(P, m, s, (unsigned long long)o->seed, idx_out, p_out, err);
-    count_launch(10);
-    LSQ_CUDA(cudaGetLastError());
-    return read_dev_error(err, st);
+    return sample_launch<DT>(A, o, s, idx_out, p_out, colscale_out, base, st);
 }
 
 }  // namespace lsq
@@ -514,6 +487,12 @@ extern "C" void lsq_default_opts(lsq_opts* o) {
     o->seed = 0;
     o->inner_tol = 0.0;
     o->grid_ctas = 0;
+}
+
+extern "C" lsq_status lsq_set_wait_limit(int64_t max_polls) {
+    LSQ_CHECK_ARG(max_polls >= 0 && max_polls <= ((int64_t)1 << 31), "max_polls must lie in [0, 2^31]");
+    g_wait_polls.store((uint32_t)max_polls, std::memory_order_relaxed);
+    return LSQ_OK;
 }
 
 extern "C" int64_t lsq_sample_size(int64_t n, double C) {

@@ -5,6 +5,8 @@ It must give exactly what lsq_sample_rows gives, call after call, although every
 reuses the same array and so starts from the previous call's leftovers.  This file is
 collected last so that a run stopping at the first failure has run every other test.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
@@ -50,3 +52,28 @@ def test_static_scratch_rejects_oversize(lsq):
     with pytest.raises(lsq.L.LsqError) as e:
         lsq.lsq_sample_rows_static(lsq.Matrix(A))
     assert e.value.code == 1 and "262144" in str(e.value)
+
+
+def test_static_scratch_null_colscale_and_launch_count(lsq):
+    """colscale_out = NULL keeps the column scales inside the fixed array; the indices and
+    probabilities must not change.  Both entry points launch the same kernels, so the
+    library's launch counter must rise by the same amount for each."""
+    A = torch.from_numpy(W.gaussian_dense(5000, 64, 3)["A"]).cuda()
+    Mx = lsq.Matrix(A)
+    o = lsq.opts(seed=11)
+    n0 = lsq.launches()
+    ref_i, ref_p, _ = lsq.lsq_sample_rows(Mx, o)
+    n1 = lsq.launches()
+    s = ref_i.numel()
+    for _ in range(2):
+        idx = torch.empty(s, dtype=torch.int32, device="cuda")
+        p = torch.empty(s, dtype=torch.float64, device="cuda")
+        s_out = C.c_int64(0)
+        code = lsq.L.load().lsq_sample_rows_static(Mx.ref, C.byref(o), s, C.c_void_p(idx.data_ptr()),
+                                                   C.c_void_p(p.data_ptr()), None, C.byref(s_out),
+                                                   lsq._stream(None))
+        assert code == 0 and s_out.value == s
+        torch.cuda.synchronize()
+        assert torch.equal(idx, ref_i) and torch.equal(p, ref_p)
+    n2 = lsq.launches()
+    assert n1 - n0 == 9 and n2 - n1 == 2 * (n1 - n0)

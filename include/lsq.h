@@ -164,9 +164,13 @@ LSQ_API lsq_status lsq_sample_rows(const lsq_matrix* A, const lsq_opts* o, int64
  *
  * Limits: A may have at most 262144 rows and 4096 columns (else LSQ_ERR_INVALID).  The
  * first call on a device looks up the array's device address (once per device, with that
- * device current), so make the first call on each device before any stream capture.  Every
- * call uses the same array: calls that overlap on the GPU (different streams, or host
- * threads) race, so serialise them.  Arguments, outputs and status as lsq_sample_rows.
+ * device current), so make the first call on each device before any stream capture.  The
+ * address is kept for the life of the process's primary context on that device: after
+ * cudaDeviceReset the library must be reloaded before this entry point is used again.
+ * Every call uses the same array and clears what it accumulates in it, so a call never
+ * depends on the previous call's leftovers; but calls that overlap on the GPU (different
+ * streams, or host threads) race, so serialise them.  colscale_out may be NULL (the scales
+ * then stay in the array).  Arguments, outputs and status as lsq_sample_rows.
  */
 LSQ_API lsq_status lsq_sample_rows_static(const lsq_matrix* A, const lsq_opts* o, int64_t s,
                                           int32_t* idx_out, double* p_out, double* colscale_out,
@@ -328,6 +332,17 @@ LSQ_API const char* lsq_last_error_string(void);
 
 /* Number of kernels this library launched since load (for launch accounting). */
 LSQ_API int64_t lsq_kernel_launch_count(void);
+
+/* Cap on every device-side wait of the library (a diagnostic and test setting; not in the
+ * paper).  Each wait polls at most max_polls times: the grid barriers of the persistent PCG
+ * kernel (default 2^26 polls), the dependency waits of the sparse Gauss-Seidel sweeps of
+ * Alg. 3 and of the level schedule builder (default 2^22).  0 restores the defaults.  A wait
+ * that runs out records a timeout in the call's device error word, every other wait of that
+ * launch then gives up as well, the kernel returns, and the call reports LSQ_ERR_TIMEOUT;
+ * the outputs of that call are then undefined, the context stays usable and nothing needs
+ * resetting.  Process-wide, read at each kernel launch.  LSQ_ERR_INVALID unless
+ * 0 <= max_polls <= 2^31. */
+LSQ_API lsq_status lsq_set_wait_limit(int64_t max_polls);
 
 #ifdef __cplusplus
 }

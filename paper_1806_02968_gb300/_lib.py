@@ -65,6 +65,7 @@ PROTOTYPES = {
     "lsq_status_string": (C.c_char_p, [C.c_int]),
     "lsq_last_error_string": (C.c_char_p, []),
     "lsq_kernel_launch_count": (I64, []),
+    "lsq_set_wait_limit": (C.c_int, [I64]),
 }
 
 _lock = threading.Lock()

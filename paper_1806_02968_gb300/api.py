@@ -266,6 +266,11 @@ def launches() -> int:
     return int(L.load().lsq_kernel_launch_count())
 
 
+def set_wait_limit(max_polls: int = 0):
+    """Cap every device-side wait at max_polls polls (0: the library's defaults)."""
+    _check(L.load().lsq_set_wait_limit(int(max_polls)), "lsq_set_wait_limit")
+
+
 def solve(A: Matrix, b, o=None, stream=None):
     """Alg. 2 end to end: sample, build the preconditioner, PCG. Returns (x, Info, extras)."""
     o = o or opts()

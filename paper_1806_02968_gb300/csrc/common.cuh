@@ -19,6 +19,17 @@ namespace lsq {
 void set_error(const std::string& msg);
 extern std::atomic<int64_t> g_launches;
 inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// Cap on the polls of a device-side wait (lsq_set_wait_limit; 0 = the defaults below).
+// Kernels receive it as an argument when they are launched.
+extern std::atomic<uint32_t> g_wait_polls;
+inline unsigned dep_wait_polls() {       // dependency waits of the sparse sweeps and levels
+    const uint32_t v = g_wait_polls.load(std::memory_order_relaxed);
+    return v ? v : (1u << 22);
+}
+inline unsigned barrier_wait_polls() {   // grid barriers of the persistent PCG kernel
+    const uint32_t v = g_wait_polls.load(std::memory_order_relaxed);
+    return v ? v : (1u << 26);
+}
 
 #define LSQ_CHECK_ARG(cond, msg)                                   \
     do {                                                           \

@@ -113,6 +113,7 @@ static lsq_status solve_columns(const lsq_matrix* A, const lsq_precond* P, const
         a.inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.0;
         a.maxit = o->maxit; a.max_outer = o->max_outer;
         a.out_i = wk.out_i; a.out_d = wk.out_d;
+        a.max_polls = barrier_wait_polls();
         int G = 0;
         lsq_status ls = dt == LSQ_F64 ? launch_pcg_f64(nmax, P->op_dtype, a, o->grid_ctas, st, &G)
                       : dt == LSQ_F32 ? launch_pcg_f32(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G)

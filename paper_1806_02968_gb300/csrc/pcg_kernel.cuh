@@ -43,6 +43,7 @@ struct PcgArgs {
     int32_t maxit, max_outer;
     int32_t* out_i;        // iters, outer, converged, status
     double* out_d;         // relres_rec, relres_true, relres_raw
+    unsigned max_polls = 1u << 26;   // bound of every grid-barrier wait
 };
 
 __device__ __forceinline__ int64_t imin64(int64_t x, int64_t y) { return x < y ? x : y; }
@@ -592,7 +593,7 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
     const char* mv_src = reinterpret_cast<const char*>(a.vals) + r0 * (int64_t)gmv.row_bytes;
 #define LSQ_BARRIER()                                   \
     do {                                                \
-        if (!grid_barrier(a.bar, G, a.err)) {           \
+        if (!grid_barrier(a.bar, G, a.err, a.max_polls)) { \
             ring_drain(ring);                           \
             return;                                     \
         }                                               \

@@ -60,6 +60,7 @@ struct SpArgs {
     SpState* S;
     double tol, inner_tol;
     int32_t maxit;
+    unsigned max_polls = 1u << 22;   // bound of every dependency wait
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
             for (int c = 0; c < 8; ++c) missing = missing || (kk[c] >= 0 && u[c] == SWEEP_EMPTY);
             if (!missing) break;
             ++polls;
-            if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+            if (polls > a.max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
                 ok = false;
                 atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 #pragma unroll
@@ -555,6 +556,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     SpState* S = (SpState*)(base + o_S);
     double* vec = (double*)(base + o_vec);
     SpArgs a{};
+    a.max_polls = dep_wait_polls();
     a.m = m; a.n = n; a.row_ptr = A->row_ptr; a.col_idx = A->col_idx;
     a.vals = A->vals;
     a.vals_res = res64 ? (DT == LSQ_F64 ? A->vals : (const void*)A->vals_f64) : A->vals;
@@ -773,6 +775,7 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     LSQ_CUDA(sc.alloc(off, st));
     char* base = sc.as<char>();
     SpArgs a{};
+    a.max_polls = dep_wait_polls();
     a.n = n;
     a.mptr = SH->mptr; a.mcol = SH->mcol; a.mdiag = SH->mdiag;
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;

@@ -73,6 +73,7 @@ struct BkArgs {
     BkState* S;
     double tol, inner_tol;
     int32_t maxit;
+    unsigned max_polls = 1u << 22;   // bound of every dependency wait
 };
 
 // Thread t holds v for column t % GK; out[c] = that column's sum over the block (fixed order).
@@ -303,7 +304,7 @@ __device__ __forceinline__ void bk_stv(double* p, double v) {
 // Loads N values (use[i] false: skipped), polling the missing ones until all are written.
 template <int N>
 __device__ __forceinline__ bool bk_gather_ready(const double* const* ptr, const bool* use, double* out,
-                                                unsigned* err) {
+                                                unsigned* err, unsigned max_polls) {
     unsigned long long u[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) u[i] = use[i] ? bk_ldv(ptr[i]) : 0ull;
@@ -315,7 +316,7 @@ __device__ __forceinline__ bool bk_gather_ready(const double* const* ptr, const 
         for (int i = 0; i < N; ++i) missing = missing || (use[i] && u[i] == BK_EMPTY);
         if (!missing) break;
         ++polls;
-        if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
+        if (polls > max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
             atomicOr(err, DEV_ERR_TIMEOUT);
             ok = false;
 #pragma unroll
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, co
                     use[i] = col_ok && t0 + i < cnt;
                     ptr[i] = e_new + (int64_t)k * K + lane;
                 }
-                bk_gather_ready<8>(ptr, use, val, &a.S->err);
+                bk_gather_ready<8>(ptr, use, val, &a.S->err, a.max_polls);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) acc = fma(mk[i], val[i], acc);
             }
@@ -440,7 +441,7 @@ __device__ __forceinline__ void bk_entry(const BkArgs& a, const double* e_new, i
         for (int c = 0; c < KT; ++c) missing = missing || (c < K && u[c] == BK_EMPTY);
         if (!missing) break;
         ++polls;
-        if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+        if (polls > a.max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
             atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 #pragma unroll
             for (int c = 0; c < KT; ++c) if (u[c] == BK_EMPTY) u[c] = 0ull;
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r
                 for (int u = 0; u < BK_PFC; ++u) missing = missing || f[u] < epoch;
                 if (!missing) break;
                 ++polls;
-                if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+                if (polls > a.max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
                     atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
                     break;
                 }
@@ -782,6 +783,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     BkState* S = (BkState*)(base + o_S);
     double* vec = (double*)(base + o_vec);
     BkArgs a{};
+    a.max_polls = dep_wait_polls();
     a.m = m; a.n = n; a.K = K; a.GK = GK;
     a.row_ptr = A->row_ptr; a.col_idx = A->col_idx; a.vals = A->vals;
     a.vals_res = res64 ? (DT == LSQ_F64 ? A->vals : (const void*)A->vals_f64) : A->vals;

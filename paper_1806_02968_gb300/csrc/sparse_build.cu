@@ -412,7 +412,8 @@ __device__ __forceinline__ void st_release_i32(int* p, int v) {
 }
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_levels(int64_t n, const int64_t* mptr, const int32_t* mcol,
-                                                const int64_t* mdiag, int* lev1, int* maxlev, unsigned* err) {
+                                                const int64_t* mdiag, int* lev1, int* maxlev, unsigned* err,
+                                                unsigned max_polls) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(256) k_levels(int64_t n, const int64_t* mptr, 
                 for (int u = 0; u < 8; ++u) missing = missing || v[u] == 0;
                 if (!missing) break;
                 ++polls;
-                if (polls > (1u << 22) || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
+                if (polls > max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
                     atomicOr(err, DEV_ERR_TIMEOUT);
 #pragma unroll
                     for (int u = 0; u < 8; ++u) v[u] = max(v[u], 1);
@@ -493,7 +494,8 @@ static lsq_status device_levels(const SparseHandle* S, int64_t n, int32_t** sche
     const int64_t* mptr = S->mptr;
     const int32_t* mcol = S->mcol;
     const int64_t* mdiag = S->mdiag;
-    void* params[] = {&nn, (void*)&mptr, (void*)&mcol, (void*)&mdiag, &lev1, &maxlev, &err};
+    unsigned max_polls = dep_wait_polls();
+    void* params[] = {&nn, (void*)&mptr, (void*)&mcol, (void*)&mdiag, &lev1, &maxlev, &err, &max_polls};
     LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)k_levels<FWD>, dim3(sms * per), dim3(256), params, 0, st));
     count_launch();
     int hmax[2] = {0, 0};

@@ -181,3 +181,13 @@ def test_binding_rejects_host_tensors_before_calling_the_library(lsq):
         lsq.lsq_pcg_solve(types.SimpleNamespace(n=3), None, torch.zeros(8, dtype=torch.float64))
     with pytest.raises(KeyError):
         lsq.opts(no_such_option=1)
+
+
+def test_wait_limit_argument_checks(lsq):
+    """lsq_set_wait_limit takes 0 (the defaults) up to 2^31 polls; it touches no device."""
+    for bad in (-1, (1 << 31) + 1):
+        with pytest.raises(lsq.L.LsqError) as e:
+            lsq.set_wait_limit(bad)
+        assert e.value.code == 1
+    lsq.set_wait_limit(1 << 31)
+    lsq.set_wait_limit(0)

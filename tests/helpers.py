@@ -69,30 +69,44 @@ def _permuted_rows(mat, perm):
             "col_idx": ci[take].astype(np.int32), "vals": v[take].astype(np.float64)}
 
 
-def _numpy_pcg_iters(orc, mat, d, Mo, b, tol, sweeps, maxit, max_outer):
+def _numpy_pcg_iters(orc, mat, d, Mo, b, tol, sweeps, maxit, max_outer, blocks=0):
     """The same PCG (restarts from the true residual included) with every product in
     numpy's BLAS summation order and p^T w taken as ||Â p||^2, which equals it in exact
-    arithmetic.  Returns the number of products Â^T Â p."""
+    arithmetic.  With blocks > 0 the sums over the rows of Â^T q are taken as partial sums
+    over `blocks` contiguous row blocks, combined pairwise (the shape of the GPU's
+    reduction: a partial per thread block, then a tree).  Returns the number of products
+    Â^T Â p."""
     import scipy.sparse as sps
     if mat["kind"] == "dense":
         Ah = np.asarray(mat["A"], np.float64) / d
     else:
         A = sps.csr_matrix((mat["vals"], mat["col_idx"], mat["row_ptr"]), shape=(mat["m"], mat["n"]))
         Ah = (A @ sps.diags(1.0 / d)).tocsr()
+    m = Ah.shape[0]
+
+    def ATq(q):
+        if blocks <= 0:
+            return Ah.T @ q
+        B = -(-m // blocks)
+        parts = [Ah[i:i + B].T @ q[i:i + B] for i in range(0, m, B)]
+        while len(parts) > 1:
+            parts = [parts[i] + parts[i + 1] if i + 1 < len(parts) else parts[i] for i in range(0, len(parts), 2)]
+        return parts[0]
+
     P = (lambda v: orc.sgs_apply(Mo, v, sweeps)) if sweeps > 0 else (lambda v: v.copy())
-    h = Ah.T @ b
+    h = ATq(b)
     hn = np.linalg.norm(h)
     y = np.zeros(h.shape[0])
     it = 0
     for outer in range(max_outer):
-        g = Ah.T @ (b - Ah @ y)
+        g = ATq(b - Ah @ y)
         if np.linalg.norm(g) <= tol * hn or it >= maxit:
             break
         z = P(g)
         p, rho = z.copy(), g @ z
         while it < maxit:
             q = Ah @ p
-            w = Ah.T @ q
+            w = ATq(q)
             alpha = rho / (q @ q)
             y += alpha * p
             g -= alpha * w
@@ -109,9 +123,11 @@ def _numpy_pcg_iters(orc, mat, d, Mo, b, tol, sweeps, maxit, max_outer):
 def rounding_variant_iters(orc, mat, smp, Mo, b, tol, sweeps=1, maxit=1000000, max_outer=20, nperm=2):
     """Iteration counts of equally valid FP64 evaluations of the same PCG on the same
     problem (same D, same sampled A_s^T A_s): the oracle on row-permuted copies of A and b
-    (only the summation order of the products changes), and a numpy evaluation in BLAS
-    order with p^T w = ||Â p||^2 (the form the fused pass computes).  Their spread around
-    the oracle's own count is the rounding sensitivity of CG on this problem."""
+    (only the summation order of the products changes), a numpy evaluation in BLAS order
+    with p^T w = ||Â p||^2 (the form the fused pass computes), and the same with the sums
+    over rows taken as 152 block partials combined pairwise (the reduction shape of the GPU
+    path, more accurate than one sequential sum over m rows).  Their spread around the
+    oracle's own count is the rounding sensitivity of CG on this problem."""
     b = np.asarray(b, np.float64)
     m = int(smp.mat.m)
     rng = np.random.default_rng(12345)
@@ -123,6 +139,7 @@ def rounding_variant_iters(orc, mat, smp, Mo, b, tol, sweeps=1, maxit=1000000, m
                         max_outer=max_outer, sweeps=sweeps)
         out.append(int(oi["iters"]))
     out.append(_numpy_pcg_iters(orc, mat, smp.d, Mo, b, tol, sweeps, maxit, max_outer))
+    out.append(_numpy_pcg_iters(orc, mat, smp.d, Mo, b, tol, sweeps, maxit, max_outer, blocks=152))
     return out
 
 

@@ -4,10 +4,16 @@ The GPU path evaluates the same PCG (Alg. 2 step 4) with other summation orders 
 split over thread blocks, lanes and warps) and with p^T w taken as ||Â p||^2.  These tests
 measure the spread of equally valid FP64 evaluations around the oracle's count on the
 same problem (same D, same sampled A_s^T A_s): the oracle on row-permuted copies of A and
-b, and a numpy evaluation in BLAS order with the ||Â p||^2 form.  On a well-conditioned
-problem every evaluation takes the same number of iterations; at kappa(Â^T Â) = 1e4 and
-1e6 they do not, which is why the GPU parity tests allow, there and only there, twice
-this measured spread instead of +-2.
+b, a numpy evaluation in BLAS order with the ||Â p||^2 form, and the same with the sums
+over rows taken as block partials combined pairwise (the GPU's reduction shape).  On a
+well-conditioned problem every evaluation takes the same number of iterations; at
+kappa(Â^T Â) = 1e4 and 1e6 they do not, which is why the GPU parity tests allow, there and
+only there, twice this measured spread instead of +-2.
+
+The oracle's own evaluation, one sequential sum over all m rows per column, is the least
+accurate of them, and finite-precision CG pays for lost accuracy with iterations: at
+kappa(Â^T Â) = 1e6 the blocked FP64 sums take about 10 % fewer iterations than the oracle,
+and an 80-bit extended-precision evaluation fewer still.
 """
 import numpy as np
 import pytest
@@ -38,7 +44,7 @@ def test_spread_at_kappa_1e4_cg(orc):
     it, vs, smp, Mo, b, y = _spread(orc, mat, 21, 1e-3, 0)
     spread = max(abs(v - it) for v in vs)
     # measured: oracle 205, row permutations 204 and 205, BLAS order with ||Â p||^2: 201
-    assert 2 <= spread <= 0.05 * it, (it, vs)
+    assert 2 <= spread <= 0.1 * it, (it, vs)
 
 
 def test_spread_at_kappa_1e6_sgs(orc):
@@ -46,9 +52,11 @@ def test_spread_at_kappa_1e6_sgs(orc):
     mat = W.udv_dense(16384, 64, 1e3, 2)
     it, vs, smp, Mo, b, y = _spread(orc, mat, 1002, 1e-6, 1)
     spread = max(abs(v - it) for v in vs)
-    # measured: oracle 317, row permutations 321 and 313, BLAS order with ||Â p||^2: 306
+    # measured: oracle 317, row permutations 321 and 313, BLAS order with ||Â p||^2: 306,
+    # blocked sums: 284 (the GPU's FP64 count on this problem)
     assert spread > 2, (it, vs)          # +-2 cannot hold here for any evaluation order
-    assert spread <= 0.06 * it, (it, vs)
+    assert spread <= 0.15 * it, (it, vs)
+    assert vs[-1] < it                   # the more accurate blocked sums converge sooner
     # the solutions of the evaluations still agree to the solution bar
     perm = np.random.default_rng(3).permutation(mat["A"].shape[0])
     y2, _ = orc.pcg(orc.as_mat({"kind": "dense", "A": mat["A"][perm]}), smp.d, Mo, b=b[perm],

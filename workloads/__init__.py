@@ -127,17 +127,36 @@ def sparse_random(m: int, n: int, nnz_per_row: int, seed: int,
         if dup_rows.size == 0:
             break
         cols[dup_rows] = rng.integers(0, n, size=(dup_rows.size, k), dtype=np.int64)
-    rows = np.repeat(np.arange(m, dtype=np.int64), k)
-    cols = cols.reshape(-1)
     extra_rows = rng.integers(0, m, size=n, dtype=np.int64)
     extra_cols = np.arange(n, dtype=np.int64)
-    key = rows * n + cols
-    present = np.isin(extra_rows * n + extra_cols, key)
-    rows = np.concatenate([rows, extra_rows[~present]])
-    cols = np.concatenate([cols, extra_cols[~present]])
+    present = (cols[extra_rows] == extra_cols[:, None]).any(axis=1)
+    er, ec = extra_rows[~present], extra_cols[~present]
     scale = 10.0 ** rng.uniform(-log10_scale, log10_scale, size=m)
-    vals = rng.standard_normal(rows.size) * scale[rows]
-    return _csr_from_coo(m, n, rows, cols, vals)
+    nb = m * k
+    z = rng.standard_normal(nb + er.size)   # the k entries of every row in turn, then the extras
+    vb = z[:nb].reshape(m, k) * scale[:, None]
+    ve = z[nb:] * scale[er]
+    # CSR with sorted columns: sort each row's k entries, then merge the extra entries (at
+    # most one per column, so at most n of them) into their rows
+    order = np.argsort(cols, axis=1, kind="stable")
+    cs = np.take_along_axis(cols, order, axis=1)
+    vs = np.take_along_axis(vb, order, axis=1)
+    eo = np.lexsort((ec, er))
+    er, ec, ve = er[eo], ec[eo], ve[eo]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(k + np.bincount(er, minlength=m), out=row_ptr[1:])
+    # slot of an extra entry: its row's start + the row's smaller base columns + the row's
+    # earlier extra entries
+    pos_e = row_ptr[er] + (cs[er] < ec[:, None]).sum(axis=1) + (np.arange(er.size) - np.searchsorted(er, er))
+    nnz = int(row_ptr[-1])
+    col_idx = np.empty(nnz, dtype=np.int64)
+    vals = np.empty(nnz, dtype=np.float64)
+    base = np.ones(nnz, dtype=bool)
+    base[pos_e] = False
+    col_idx[pos_e], vals[pos_e] = ec, ve
+    col_idx[base], vals[base] = cs.reshape(-1), vs.reshape(-1)
+    return {"kind": "csr", "m": int(m), "n": int(n), "row_ptr": row_ptr,
+            "col_idx": col_idx.astype(np.int32), "vals": vals}
 
 
 def graph_incidence(n_nodes: int, n_edges: int, seed: int,

@@ -343,6 +343,12 @@ struct Ring {
     const char* pre_src;  // stages already in flight for a pass starting at pre_src
     uint32_t pre_stage;
     int pre_count;
+    // split pass (row_pass_split): "q of this stage is ready" and "slot is free" barriers,
+    // with their parity bits, and the per-stage q values (RING_SLOTS x 16 double-floats)
+    uint64_t* qbars;
+    uint64_t* ebars;
+    uint32_t qphase, ephase;
+    f2* s_q;
 };
 // Stage geometry of a pass: rows per warp (2 when four stages of 2 rows per warp fit),
 // rows per stage R, slots in the ring (>= 3 unless a row is very long).
@@ -485,11 +491,179 @@ __device__ __forceinline__ bool row_pass_rpw(const PcgArgs& a, const void* vals,
     return ok;
 }
 
+// The fused pass w = Â^T (Â p) for double-float values with the warps split by role, for
+// stages of 16 rows (NMAX = 256 or 512, 16 warps):
+//   warps 0-7  ("dot" warps) take two rows of each stage, compute q_i = â_i . p̃ for both in
+//              double-float, reduce the two sums together, put q_i in s_q and arrive on the
+//              stage's q barrier;
+//   warps 8-15 ("axpy" warps) wait for q, and lane l of axpy warp v accumulates the columns
+//              j = v NMAX/8 + l CPL + {0..CPL-1} of w over all 16 rows of the stage
+//              (CPL = NMAX/256 columns per lane); they then arrive on the stage's empty
+//              barrier, and lane 0 of warp 8 refills the slot with a later stage.
+// No block-wide barrier inside the pass: each role waits only for the data it needs.  A
+// column of w is owned by one lane for the whole pass, so its partial needs no cross-warp
+// reduction; the sum of q_i^2 is reduced over the dot warps in a fixed order.  Every wait is
+// bounded (a wait that gives up sets the error word; the roles still arrive so that the
+// others' waits end).
+template <int NMAX, bool FULL>
+__device__ __forceinline__ bool row_pass_split(const PcgArgs& a, const void* vals, const double* s_v,
+                                               void* s_vc_raw, double* s_scal, int64_t r0, int64_t r1,
+                                               Ring& ring, const Geo g) {
+    constexpr int CPL = NMAX / 256;           // columns per axpy lane
+    constexpr int NCH = NMAX / 64;            // 64-column chunks of a row (two per lane)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n = a.n;
+    f2* s_vc = reinterpret_cast<f2*>(s_vc_raw);
+    for (int j = threadIdx.x; j < NMAX; j += blockDim.x) s_vc[j] = df_from_double(s_v[j]);
+    const int nrows = (int)(r1 - r0);
+    const int nst = (nrows + 15) / 16;
+    const char* src = reinterpret_cast<const char*>(vals) + r0 * (int64_t)g.row_bytes;
+    int have = 0;
+    if (ring.pre_count > 0) {
+        if (ring.pre_src == src && ring.pre_stage == g.stage_bytes) have = ring.pre_count;
+        else ring_drain(ring);
+    }
+    ring.pre_count = 0;
+    __syncthreads();   // s_vc ready; previous users of the ring are done
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        for (int i = have; i < nst && i < g.slots; ++i)
+            ring_issue(ring, i, g, src + (int64_t)i * g.stage_bytes,
+                       (uint32_t)min(16, nrows - i * 16) * g.row_bytes);
+    }
+    bool ok = true;
+    if (wid < 8) {
+        // ---- dot warps: rows 2 wid and 2 wid + 1 of every stage
+        f2 qs{0.f, 0.f};
+        int slot = 0;
+        for (int i = 0; i < nst; ++i) {
+            if (ok && !mbar_wait(&ring.bars[slot], (ring.phase >> slot) & 1u)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);   // the shuffles below need the whole warp
+            const int rows_here = min(16, nrows - i * 16);
+            const int lr = 2 * wid;
+            f2 q0{0.f, 0.f}, q1{0.f, 0.f};
+            if (ok && lr < rows_here) {
+                const bool has1 = lr + 1 < rows_here;
+                const float* p0 = reinterpret_cast<const float*>(ring.buf + slot * g.stage_bytes + lr * g.row_bytes);
+                const float* p1 = has1 ? p0 + g.row_bytes / 4 : p0;
+                f2 d0[4], d1[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { d0[k] = f2{0.f, 0.f}; d1[k] = f2{0.f, 0.f}; }
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const int col = c * 64 + lane * 2;
+                    float4 sx = *reinterpret_cast<const float4*>(s_vc + col);   // p̃ (hi, lo) x 2
+                    float4 v = *reinterpret_cast<const float4*>(p0 + 2 * col);   // row 0, 2 values
+                    float4 w = *reinterpret_cast<const float4*>(p1 + 2 * col);   // row 1
+                    if (!FULL) {
+                        // columns beyond n (row padding) never enter the sums
+                        if (col >= n) { v = make_float4(0.f, 0.f, 0.f, 0.f); w = v; }
+                        else if (col + 1 >= n) { v.z = v.w = 0.f; w.z = w.w = 0.f; }
+                    }
+                    const int k0 = (c & 1) * 2;
+                    df_fma_cascade(d0[k0], f2{v.x, v.y}, f2{sx.x, sx.y});
+                    df_fma_cascade(d0[k0 + 1], f2{v.z, v.w}, f2{sx.z, sx.w});
+                    df_fma_cascade(d1[k0], f2{w.x, w.y}, f2{sx.x, sx.y});
+                    df_fma_cascade(d1[k0 + 1], f2{w.z, w.w}, f2{sx.z, sx.w});
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { d0[k] = df_norm(d0[k]); d1[k] = df_norm(d1[k]); }
+                df_add(d0[0], d0[1]); df_add(d0[2], d0[3]); df_add(d0[0], d0[2]);
+                df_add(d1[0], d1[1]); df_add(d1[2], d1[3]); df_add(d1[0], d1[2]);
+                q0 = d0[0]; q1 = d1[0];
+                pair_reduce2<f2>(q0, q1, lane, [](f2& x, f2 y) { df_add(x, y); }, shfl_f2, bcast_f2);
+                if (!has1) q1 = f2{0.f, 0.f};
+            }
+            if (lane == 0) {
+                ring.s_q[slot * 16 + lr] = q0;
+                ring.s_q[slot * 16 + lr + 1] = q1;
+                df_fma(qs, q0, q0);
+                df_fma(qs, q1, q1);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ring.qbars[slot]);
+            ring.phase ^= (1u << slot);
+            ring.qphase ^= (1u << slot);
+            ring.ephase ^= (1u << slot);
+            slot = (slot + 1 == g.slots) ? 0 : slot + 1;
+        }
+        if (lane == 0) s_scal[wid] = df_to_double(qs);
+    } else {
+        // ---- axpy warps: CPL columns per lane, every row of every stage
+        const int aw = wid - 8;
+        const int col0 = aw * (NMAX / 8) + lane * CPL;
+        const bool live = FULL || col0 < n;
+        f2 acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = f2{0.f, 0.f};
+        int slot = 0;
+        for (int i = 0; i < nst; ++i) {
+            if (ok && !mbar_wait(&ring.qbars[slot], (ring.qphase >> slot) & 1u)) ok = false;
+            if (ok && !mbar_wait(&ring.bars[slot], (ring.phase >> slot) & 1u)) ok = false;
+            const int rows_here = min(16, nrows - i * 16);
+            if (ok && live) {
+                const char* base = ring.buf + slot * g.stage_bytes + (size_t)col0 * 8;
+                const f2* q = ring.s_q + slot * 16;
+                for (int r = 0; r < rows_here; ++r) {
+                    const f2 qr = q[r];
+                    const float* rp = reinterpret_cast<const float*>(base + r * g.row_bytes);
+                    if (CPL == 1) {
+                        const float2 v = *reinterpret_cast<const float2*>(rp);
+                        df_fma_cascade(acc[0], qr, f2{v.x, v.y});
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < CPL; c += 2) {
+                            const float4 v = *reinterpret_cast<const float4*>(rp + 2 * c);
+                            df_fma_cascade(acc[c], qr, f2{v.x, v.y});
+                            df_fma_cascade(acc[c + 1], qr, f2{v.z, v.w});
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ring.ebars[slot]);
+            // lane 0 of warp 8: refill this slot once all 8 axpy warps are done with it
+            if (aw == 0 && lane == 0 && i + g.slots < nst) {
+                if (ok && !mbar_wait(&ring.ebars[slot], (ring.ephase >> slot) & 1u)) ok = false;
+                if (ok) {
+                    fence_proxy_async_smem();
+                    const int k = i + g.slots;
+                    ring_issue(ring, slot, g, src + (int64_t)k * g.stage_bytes,
+                               (uint32_t)min(16, nrows - k * 16) * g.row_bytes);
+                }
+            }
+            ring.phase ^= (1u << slot);
+            ring.qphase ^= (1u << slot);
+            ring.ephase ^= (1u << slot);
+            slot = (slot + 1 == g.slots) ? 0 : slot + 1;
+        }
+        double* pw = a.part_w + (int64_t)blockIdx.x * n;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+            if (FULL || col0 + c < n) pw[col0 + c] = df_to_double(df_norm(acc[c]));
+    }
+    if (!ok) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += s_scal[w];
+        a.part_s[(int64_t)blockIdx.x * PART_S + 0] = t;
+    }
+    __syncthreads();
+    return ok;
+}
+
 template <int DT, int NMAX, int MODE>
 __device__ __forceinline__ bool row_pass(const PcgArgs& a, const void* vals, const double* s_v,
                                          void* s_vc_raw, double* s_scal, int64_t r0, int64_t r1,
                                          Ring& ring) {
     const Geo g = geometry(a.ld, RowOps<DT, NMAX>::ES, blockDim.x >> 5, ring.bytes);
+    if constexpr (DT == LSQ_F32X2 && MODE == PASS_MATVEC && (NMAX == 256 || NMAX == 512)) {
+        if (g.rpw == 1 && g.R == 16 && g.slots >= 2 && blockDim.x == 512) {
+            if (a.n == NMAX) return row_pass_split<NMAX, true>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
+            return row_pass_split<NMAX, false>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
+        }
+    }
     if (g.rpw == 2) return row_pass_rpw<DT, NMAX, MODE, 2>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
     return row_pass_rpw<DT, NMAX, MODE, 1>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
 }
@@ -568,17 +742,24 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
     extern __shared__ __align__(128) char smem_raw[];
     __shared__ double s_scal[64];
     __shared__ __align__(8) uint64_t s_bars[RING_SLOTS];
+    __shared__ __align__(8) uint64_t s_qbars[RING_SLOTS];
+    __shared__ __align__(8) uint64_t s_ebars[RING_SLOTS];
+    __shared__ __align__(16) f2 s_q[RING_SLOTS * 16];
     const int64_t n = a.n;
     const int nwarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31;
     const int RB = ring_bytes(NMAX);
-    Ring ring{smem_raw, s_bars, 0u, RB, nullptr, 0u, 0};
+    Ring ring{smem_raw, s_bars, 0u, RB, nullptr, 0u, 0, s_qbars, s_ebars, 0u, 0u, s_q};
     double* s_p = reinterpret_cast<double*>(smem_raw + RB);  // NMAX: p (replicated)
     double* s_v = s_p + NMAX;        // NMAX: D^{-1} x vector for the row pass, or g
     double* s_vc = s_v + NMAX;       // NMAX: s_v in the compute type of the row pass
     double* s_invd = s_vc + NMAX;    // NMAX: 1 / d_j
     if (threadIdx.x == 0) {
-        for (int i = 0; i < RING_SLOTS; ++i) mbar_init(&s_bars[i], 1);
+        for (int i = 0; i < RING_SLOTS; ++i) {
+            mbar_init(&s_bars[i], 1);
+            mbar_init(&s_qbars[i], 8);   // the 8 dot warps of row_pass_split
+            mbar_init(&s_ebars[i], 8);   // the 8 axpy warps
+        }
         fence_mbar_init();
     }
     for (int64_t j = threadIdx.x; j < NMAX; j += blockDim.x) {

@@ -15,6 +15,7 @@ written, FP64, single thread) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -52,7 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
     ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch"], default="udv",
-                    help="udv: the timed benchmark; the others measure the CSR configurations")
+                    help="udv: the timed benchmark; the others measure one other configuration alone")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations and the FP64 comparison solve after the timed region")
     return ap.parse_args()
 
 
@@ -211,14 +214,82 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args, args.m, args.n),
-                       "tol": args.tol, "sweeps": args.sweeps, "s": math.ceil(4 * args.n * math.log(args.n))},
+            "config": {"workload": workload_name(args, args.m, args.n), "m": args.m, "n": args.n,
+                       "kappa": args.kappa, "tol": args.tol, "sweeps": args.sweeps,
+                       "s": math.ceil(4 * args.n * math.log(args.n)), "mode": args.mode,
+                       "l2": "inputs larger than L2 (A is %.2f GB)" % (args.m * args.n * 8 / 1e9),
+                       "parallelism": "replicas1"},
             "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle setup (sampling, A_s^T A_s, SGS) on the full matrix + "
                                        f"{args.cpu_iters} PCG iterations per step, extrapolated to "
                                        f"{iters_assumed} iterations"},
             "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def gauss_config(steps=50, warmup=10, cpu=True):
+    """The Gaussian dense configuration: A 4096 x 128 N(0,1), b = A x* + 1e-3 noise, FP64,
+    s = ceil(4 n ln n), one forward + one backward sweep, tol 1e-10.  A step is sampling, the
+    preconditioner and the solve; steps are timed with CUDA events on the stream (A, 4 MB,
+    stays in L2, so the roofline fraction is of HBM bandwidth for a kernel that does not
+    need it)."""
+    import torch
+    import workloads as W
+    from paper_1806_02968_gb300 import api
+    mat = W.gaussian_dense(4096, 128, 2)
+    xs, b = W.rhs_for(mat, 1, 1e-3, 102)
+    A = torch.from_numpy(mat["A"]).cuda()
+    bd = torch.from_numpy(b[0]).cuda()
+    Mx = api.Matrix(A)
+    o = api.opts(seed=1002)
+    stream = torch.cuda.current_stream()
+    pcg = []
+
+    def step():
+        idx, p, d = api.lsq_sample_rows(Mx, o)
+        P = api.lsq_build_precond(Mx, idx, p, d, o)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = api.lsq_pcg_solve(Mx, P, bd, o)
+        e1.record(stream)
+        return x, info, e0, e1
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    L0 = api.launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        x, info, e0, e1 = step()
+        e1.synchronize()
+        pcg.append(e0.elapsed_time(e1))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    m, n = mat["A"].shape
+    it = int(info.iters[0])
+    byts = it * (m * n * 8 + n * n * 8) + (2 + max(int(info.outer[0]) - 1, 0)) * (m * n * 8 + 8 * m)
+    pcg_s = float(np.mean(pcg)) / 1e3
+    out = {"value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "dtype": "f64", "config": {"workload": "gaussian_dense_4096x128", "m": m, "n": n, "tol": 1e-10,
+                                      "sweeps": 1, "s": int(info.s)},
+           "iters": it, "relres_true": float(info.relres_true[0]), "converged": int(info.converged[0]),
+           "pcg_ms": float(np.mean(pcg)), "gpu_launches_per_step": (api.launches() - L0) // steps,
+           "roofline": {"bound": "hbm", "achieved": byts / pcg_s / 1e9, "peak": peaks()["hbm_gbs"],
+                        "unit": "GB/s", "frac": byts / pcg_s / 1e9 / peaks()["hbm_gbs"], "traffic": None,
+                        "kernel": "k_pcg_dense",
+                        "note": "A (4.2 MB) and the operator stay in L2: the launch is bound by its "
+                                "grid barriers, not by HBM"}}
+    if cpu:
+        import oracle
+        oracle.build()
+        c0 = time.perf_counter()
+        S = oracle.Solve(mat, b[0], seed=1002, tol=1e-10)
+        t = time.perf_counter() - c0
+        out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                               "sample": f"one complete oracle solve ({S.info['iters']} iterations)"}
+        out["oracle_iters"] = int(S.info["iters"])
+    return out
 
 
 def run_ours(args):
@@ -356,6 +427,49 @@ def run_ours(args):
                          f"({t_setup:.2f} s) + {args.cpu_iters} PCG iterations ({t_iter:.3f} s each), "
                          f"extrapolated to the GPU's {int(info.iters[0])} iterations"}
 
+    configs = None
+    if rank == 0 and not args.no_configs and args.workload == "udv":
+        configs = {}
+        # the plain FP64 GPU solve of the same problem with the same samples: the comparison
+        # point of the precision form (speed and error of every result against FP64)
+        o64 = api.opts(seed=seed_sample, tol=args.tol, maxit=args.maxit, precond_dtype=0, sweeps=args.sweeps,
+                       max_outer=50)
+        idx, p, d = api.lsq_sample_rows(M64, o64)
+        P64 = api.lsq_build_precond(M64, idx, p, d, o64)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        x64, info64 = api.lsq_pcg_solve(M64, P64, bd, o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f64_ms = f0.elapsed_time(f1)
+        err = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+        fit = float(torch.linalg.norm(A64 @ (x - x64)) / torch.linalg.norm(A64 @ x64))
+        it64 = int(info64.iters[0])
+        b64 = it64 * (m * n * 8 + n * n * 8)
+        configs[f"udv_dense_{m}x{n}_kappa{args.kappa:g}_f64"] = {
+            "value": 1e3 / f64_ms, "unit": "solves/s (PCG only)", "pcg_ms": f64_ms, "dtype": "f64",
+            "iters": it64, "relres_true": float(info64.relres_true[0]), "converged": int(info64.converged[0]),
+            "roofline": {"bound": "alu", "achieved": it64 * (4.0 * m * n + 2.0 * n * n) / (f64_ms / 1e3) / 1e12,
+                         "peak": 1.25, "unit": "TFLOP/s",
+                         "frac": it64 * (4.0 * m * n + 2.0 * n * n) / (f64_ms / 1e3) / 1e12 / 1.25,
+                         "traffic": None, "kernel": "k_pcg_dense (FP64 values)",
+                         "hbm_gbs": b64 / (f64_ms / 1e3) / 1e9},
+            "speedup_of_headline_form": f64_ms / float(np.mean(pcg_ms))}
+        err_vs_f64 = {"rel_x": err, "rel_Ax": fit, "f64_iters": it64,
+                      "note": "||x - x_f64|| / ||x_f64|| and ||A (x - x_f64)|| / ||A x_f64|| against the "
+                              "FP64 GPU solve with the same samples; both meet the relative normal-equation "
+                              "residual 1e-10, which at kappa(A) = 1e6 leaves the components along the "
+                              "smallest singular directions free up to kappa^2 tol"}
+        gc.collect()
+        torch.cuda.empty_cache()
+        configs["gaussian_dense_4096x128"] = gauss_config(cpu=not args.no_cpu_baseline)
+        for w in ("sparse", "graph", "adjoint"):
+            c = sparse_config(w, cpu=not args.no_cpu_baseline)
+            configs[c["config"]["workload"]] = c
+            gc.collect()
+            torch.cuda.empty_cache()
+        configs["uneven_dense_batch_64x16rhs"] = batch_config(cpu=not args.no_cpu_baseline)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -372,42 +486,85 @@ def run_ours(args):
                           "relres_raw": float(info.relres_raw[0]),
                           "converged": int(info.converged[0]), "pcg_ms": float(np.mean(pcg_ms)),
                           "us_per_iter": 1e3 * float(np.mean(pcg_ms)) / max(int(info.iters[0]), 1)}}
+        if configs is not None:
+            line["err_vs_f64"] = err_vs_f64
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_sparse_workload(args):
-    """CSR configurations: sparse random 4e6 x 4e4 (FP32 values, FP64 refinement), weighted
-    graph incidence with 32 right-hand sides (FP64), sparse 1e6 x 1e4 with 16 right-hand
-    sides through the solve and the adjoint (FP32 values, FP64 refinement)."""
+SPARSE_CFGS = {
+    # name: (generator, right-hand sides, noise, value type)
+    "sparse": ("sparse_random_4000000x40000_8nnz", 1, 1e-3, "f32"),
+    "graph": ("graph_incidence_262144nodes_32rhs", 32, 1e-4, "f64"),
+    "adjoint": ("sparse_random_1000000x10000_16rhs_adjoint", 16, 1e-3, "f32"),
+}
+
+
+def sparse_matrix(which):
+    import workloads as W
+    if which == "sparse":
+        return W.sparse_random(4_000_000, 40_000, 8, 3)
+    if which == "graph":
+        return W.graph_incidence(262144, 8 * 262144, 4)
+    return W.sparse_random(1_000_000, 10_000, 8, 5)
+
+
+def csr_bytes_per_iter(mat, nnz_m, es, k):
+    """Algorithmic bytes of one CSR PCG iteration: A once (values, column indices, row
+    pointers), M = A_s^T A_s once over the two sweeps (values and indices), and about ten
+    n x k FP64 vector passes."""
+    m, n = int(mat["m"]), int(mat["n"])
+    nnz_a = int(mat["row_ptr"][-1])
+    return nnz_a * (es + 4) + 8 * (m + 1) + nnz_m * (es + 4) + 8 * (n + 1) + 10 * 8 * n * k
+
+
+def oracle_csr_sample(mat, b, seed, iters_gpu, k, cpu_iters=3):
+    """Oracle (FP64, one thread) on one column of the same input: full setup (S1-S6) plus
+    cpu_iters PCG iterations, extrapolated to the GPU's iterations and k columns."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    smp = oracle.Sample(mat, seed)
+    Mo = oracle.SampledM(smp)
+    t1 = time.perf_counter()
+    oracle.pcg(smp.mat, smp.d, Mo, b=b, tol=1e-300, maxit=cpu_iters, max_outer=1)
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / cpu_iters
+    t = (t1 - t0) + per_iter * max(iters_gpu, 1) * k
+    return {"value": k / t, "unit": "solves/s (right-hand sides)", "cores": 1, "kind": "oracle",
+            "sample": f"oracle setup (sampling, A_s^T A_s) on the full matrix ({t1 - t0:.1f} s) + "
+                      f"{cpu_iters} PCG iterations of one column ({per_iter:.3f} s each), extrapolated "
+                      f"to the GPU's {iters_gpu} iterations x {k} columns"}
+
+
+def sparse_config(which, tol=1e-10, maxit=1000000, sweeps=1, inner_tol=0.0, steps=3, warmup=1,
+                  cpu=True, mat=None):
+    """One CSR configuration: sparse random 4e6 x 4e4 (FP32 values, FP64 refinement), weighted
+    graph incidence with 32 right-hand sides (FP64), or sparse 1e6 x 1e4 with 16 right-hand
+    sides through the solve and the adjoint (FP32 values, FP64 refinement).  A step is
+    sampling, the preconditioner and the solve (and the adjoint), timed with synchronising
+    host clocks around each phase."""
     import torch
     import workloads as W
-    import paper_1806_02968_gb300 as pkg
-    pkg.build()
     from paper_1806_02968_gb300 import api
-    torch.cuda.set_device(0)
-    if args.workload == "sparse":
-        mat, k, noise, dt = W.sparse_random(4_000_000, 40_000, 8, 3), 1, 1e-3, "f32"
-        name = "sparse_random_4000000x40000_8nnz"
-    elif args.workload == "graph":
-        mat, k, noise, dt = W.graph_incidence(262144, 8 * 262144, 4), 32, 1e-4, "f64"
-        name = "graph_incidence_262144nodes_32rhs"
-    else:
-        mat, k, noise, dt = W.sparse_random(1_000_000, 10_000, 8, 5), 16, 1e-3, "f32"
-        name = "sparse_random_1000000x10000_16rhs_adjoint"
+    name, k, noise, dt = SPARSE_CFGS[which]
+    mat = mat if mat is not None else sparse_matrix(which)
     xs, b = W.rhs_for(mat, k, noise, 1234)
     rp = torch.from_numpy(mat["row_ptr"]).cuda()
     ci = torch.from_numpy(mat["col_idx"]).cuda()
     v64 = torch.from_numpy(mat["vals"]).cuda()
     vals = v64.float() if dt == "f32" else v64
     Mx = api.Matrix(row_ptr=rp, col_idx=ci, vals=vals, n=mat["n"], vals_f64=v64 if dt == "f32" else None)
-    o = api.opts(seed=1003, tol=args.tol, maxit=args.maxit, max_outer=50, inner_tol=args.inner_tol, sweeps=args.sweeps,
+    o = api.opts(seed=1003, tol=tol, maxit=maxit, max_outer=50, inner_tol=inner_tol, sweeps=sweeps,
                  precond_dtype=1 if dt == "f32" else 0)
     B = torch.from_numpy(b).cuda()
-    X = None
-    res = {}
-    for rep in range(args.warmup + args.steps):
+    runs = []
+    L0 = api.launches()
+    for rep in range(warmup + steps):
+        if rep == warmup:
+            L0 = api.launches()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         idx, p, d = api.lsq_sample_rows(Mx, o)
@@ -416,31 +573,50 @@ def run_sparse_workload(args):
         torch.cuda.synchronize(); t2 = time.perf_counter()
         X, info = api.lsq_pcg_solve(Mx, P, B, o)
         torch.cuda.synchronize(); t3 = time.perf_counter()
-        extra = {}
-        if args.workload == "adjoint":
+        r = {"sample_s": t1 - t0, "build_s": t2 - t1, "solve_s": t3 - t2}
+        if which == "adjoint":
             G = 2 * (X - torch.from_numpy(xs).cuda())
             gb, gv, lam, ainfo = api.lsq_pcg_adjoint(Mx, P, X, B, G, o)
             torch.cuda.synchronize()
-            extra = {"adjoint_s": time.perf_counter() - t3, "adjoint_iters": ainfo.iters.tolist()}
-        res = {"sample_s": t1 - t0, "build_s": t2 - t1, "solve_s": t3 - t2, **extra,
-               "iters": info.iters.tolist(), "converged": info.converged.tolist(),
-               "relres_true_max": float(np.max(info.relres_true)), "nnz_A": int(mat["row_ptr"][-1]),
-               "nnz_M": int(info.nnz_M), "levels": int(info.levels), "s": int(info.s)}
+            r["adjoint_s"] = time.perf_counter() - t3
+            r["adjoint_iters_max"] = int(np.max(ainfo.iters))
+        if rep >= warmup:
+            runs.append(r)
+    launches = (api.launches() - L0) // max(steps, 1)
+    res = {key: float(np.mean([r[key] for r in runs])) for key in runs[0]}
     tot = res["sample_s"] + res["build_s"] + res["solve_s"] + res.get("adjoint_s", 0.0)
-    # solve-level HBM rate: per iteration, A read twice (row and column passes) with its indices,
-    # the dependency side of M read once per sweep (2 sweeps), and ~12 n-vector passes per column
-    it = max(1, int(np.max(info.iters)))
+    it = int(np.max(info.iters))
     es = 4 if dt == "f32" else 8
-    nnz_a, nnz_m = int(mat["row_ptr"][-1]), int(info.nnz_M)
-    per_iter = 2 * nnz_a * (es + 4) + 8 * (mat["m"] + 1) + nnz_m * (es + 4) + 12 * 8 * mat["n"] * k
-    res["solve_hbm_gbs"] = it * per_iter / res["solve_s"] / 1e9
-    res["solve_hbm_frac_of_measured"] = res["solve_hbm_gbs"] / peaks()["hbm_gbs"]
-    line = {"metric": METRIC, "value": k / tot, "unit": "solves/s (right-hand sides)", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3, "higher_is_better": True,
-            "dtype": dt + ("+f64" if dt == "f32" else ""), "data": "synthetic",
-            "config": {"workload": name, "m": int(mat["m"]), "n": int(mat["n"]), "k": k, "tol": args.tol,
-                       "sweeps": args.sweeps},
-            "phases": res}
+    per_iter = csr_bytes_per_iter(mat, int(info.nnz_M), es, k)
+    achieved = it * per_iter / res["solve_s"] / 1e9
+    out = {"value": k / tot, "unit": "solves/s (right-hand sides)", "ms_per_step": tot * 1e3,
+           "steps": steps, "warmup": warmup, "dtype": dt + ("+f64" if dt == "f32" else ""),
+           "config": {"workload": name, "m": int(mat["m"]), "n": int(mat["n"]), "k": k, "tol": tol,
+                      "sweeps": sweeps, "nnz_A": int(mat["row_ptr"][-1]), "nnz_M": int(info.nnz_M),
+                      "levels": int(info.levels), "s": int(info.s)},
+           "iters_max": it, "iters": info.iters.tolist() if k <= 4 else None,
+           "converged": int(np.sum(info.converged)), "relres_true_max": float(np.max(info.relres_true)),
+           "gpu_launches_per_step": int(launches),
+           "phases": res,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks()["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks()["hbm_gbs"], "traffic": None,
+                        "kernel": "whole CSR iteration (row and column passes, sweeps, vector kernels)",
+                        "bytes_per_iter": per_iter,
+                        "note": "algorithmic bytes per iteration (A once, M once, ~10 n x k vector "
+                                "passes) x iterations / solve time"}}
+    if cpu:
+        out["cpu_baseline"] = oracle_csr_sample(mat, b[0], 1003, it, k)
+    return out
+
+
+def run_sparse_workload(args):
+    import torch
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    torch.cuda.set_device(0)
+    out = sparse_config(args.workload, args.tol, args.maxit, args.sweeps, args.inner_tol,
+                        args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+    line = {"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
 
 
@@ -448,17 +624,19 @@ def run_sparse_workload(args):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def run_batch_workload(args):
+def batch_config(tol=1e-10, maxit=1000000, steps=5, warmup=3, cpu=True):
     """64 uneven dense Gaussian problems (m log-uniform in [1024, 16384], n in [32, 256]),
     16 right-hand sides each, FP32 values: all PCG solves in one launch (lsq_batch_solve,
     replayed from a captured CUDA graph), against the same problems solved one at a time
     with FP64 values (lsq_pcg_solve)."""
     import torch
     import workloads as W
-    import paper_1806_02968_gb300 as pkg
-    pkg.build()
     from paper_1806_02968_gb300 import api
-    torch.cuda.set_device(0)
+
+    class _A:
+        pass
+    args = _A()
+    args.tol, args.maxit, args.steps, args.warmup = tol, maxit, steps, warmup
     count, k = 64, 16
     mats = W.uneven_dense_batch(count, (1024, 16384), (32, 256), 5)
     o = api.opts(tol=args.tol, maxit=min(args.maxit, 100000), max_outer=30, inner_tol=1e-4)
@@ -542,14 +720,13 @@ def run_batch_workload(args):
     f1.record()
     torch.cuda.synchronize()
     f64_ms = f0.elapsed_time(f1)
-    line = {"metric": METRIC, "value": count * k / (solve_ms / 1e3), "unit": "solves/s (right-hand sides)",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_ms,
-            "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+    out = {"value": count * k / (solve_ms / 1e3), "unit": "solves/s (right-hand sides)",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_ms, "dtype": "f32+f64",
             "config": {"workload": "uneven_dense_batch_64x16rhs", "count": count, "k": k,
                        "m_range": [1024, 16384], "n_range": [32, 256], "tol": args.tol,
                        "A_bytes": int(sum(T.numel() * 4 for T, _, _, _ in probs)), "cluster": cluster,
                        "l2": "A (about the L2 size) stays resident across replays"},
-            "gpu_launches": kernels_per_replay * args.steps,
+            "gpu_launches_per_step": kernels_per_replay,
             "roofline": {"bound": "alu", "achieved": flops / (solve_ms / 1e3) / 1e12,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops / (solve_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
@@ -561,7 +738,31 @@ def run_batch_workload(args):
                        "relres_true_max": float(tru.max()),
                        "f64_one_at_a_time_ms": f64_ms, "f64_iters_mean": float(np.mean(f64_iters)),
                        "speedup_vs_f64_single": f64_ms / solve_ms}}
-    print(json.dumps(line), flush=True)
+    if cpu:
+        # the oracle on 4 of the 64 problems, one right-hand side each, scaled to 64 x 16
+        import oracle
+        oracle.build()
+        picks = [0, 21, 42, 63]
+        t0 = time.perf_counter()
+        for i in picks:
+            T, seen, B = keep[i]
+            S = oracle.Solve(seen, B[0].cpu().numpy(), seed=200 + i, tol=tol, max_outer=30)
+        t_cpu = (time.perf_counter() - t0) * (count / len(picks)) * k
+        out["cpu_baseline"] = {"value": count * k / t_cpu, "unit": "solves/s (right-hand sides)", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"oracle end to end (setup + FP64 PCG) on problems {picks}, one "
+                                         f"right-hand side each, scaled to {count} problems x {k} columns"}
+    return out
+
+
+def run_batch_workload(args):
+    import torch
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    torch.cuda.set_device(0)
+    out = batch_config(args.tol, args.maxit, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+    print(json.dumps({"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", **out}),
+          flush=True)
 
 
 def main():

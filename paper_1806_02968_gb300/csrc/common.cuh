@@ -127,40 +127,56 @@ __device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v
     return old;
 }
 
-// Grid-wide barrier for a cooperative launch.  `bar` points at two words: [0] arrival
-// count, [1] generation.  Spins are bounded: after `max_polls` polls the barrier records
-// DEV_ERR_TIMEOUT in *err and returns false; callers then leave the kernel.  Every CTA
-// also returns false once any CTA has recorded an error, so a stuck barrier releases the
-// whole grid.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err,
-                                             unsigned max_polls = (1u << 26)) {
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch on one monotonic 64-bit arrival count (zeroed
+// before the launch).  Every CTA passes the same sequence of barriers and counts them in
+// `epoch`; barrier number e is passed once the count reaches (e + 1) * nblocks, so the last
+// CTA to arrive is released by its own arrival and the others by one load.  The top bit of
+// the count is the grid's error flag (raise_grid_error): an arrival or a poll that sees it
+// returns false, and callers leave the kernel.  Polls are bounded: after `max_polls` the
+// barrier records DEV_ERR_TIMEOUT and returns false.
+constexpr unsigned long long BAR_ERR = 1ull << 63;
+
+__device__ __forceinline__ void raise_grid_error(unsigned* err, unsigned long long* bar, unsigned bits) {
+    atomicOr(err, bits);
+    atomicOr(bar, BAR_ERR);
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned nblocks, unsigned* err,
+                                             unsigned long long& epoch, unsigned max_polls = (1u << 26)) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const unsigned long long target = (epoch + 1ull) * nblocks;
+        unsigned long long seen = atom_add_acq_rel_u64(bar, 1ull) + 1ull;   // this CTA's writes
+        unsigned polls = 0;
         int ok = 1;
-        unsigned gen = ld_acquire_u32(bar + 1);
-        unsigned arrived = atom_add_release_u32(bar, 1u);   // release: this CTA's writes
-        if (arrived == nblocks - 1) {
-            // last to arrive: reset the count, then open the next generation
-            atomicExch(bar, 0u);
-            __threadfence();
-            atom_add_release_u32(bar + 1, 1u);
-        } else {
-            unsigned polls = 0;
-            while (ld_acquire_u32(bar + 1) == gen) {
-                if (ld_acquire_u32(err) != 0u) { ok = 0; break; }
-                if (++polls > max_polls) {
-                    atomicOr(err, DEV_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (polls > 64) __nanosleep(polls > 4096 ? 256 : 32);
+        while (true) {
+            if (seen & BAR_ERR) { ok = 0; break; }
+            if (seen >= target) break;
+            if (++polls > max_polls) {
+                raise_grid_error(err, bar, DEV_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            if (polls > 64) __nanosleep(polls > 4096 ? 256 : 32);
+            seen = ld_acquire_u64(bar);
         }
-        if (ok && ld_acquire_u32(err) != 0u) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
+    ++epoch;
     return s_ok != 0;
 }
 

@@ -108,7 +108,7 @@ static lsq_status solve_columns(const lsq_matrix* A, const lsq_precond* P, const
         a.x = X + c * ldx;
         a.y = wk.y; a.g = wk.g; a.z = wk.z;
         a.part_w = wk.part_w; a.part_s = wk.part_s;
-        a.bar = wk.bar; a.err = wk.err;
+        a.bar = reinterpret_cast<unsigned long long*>(wk.bar); a.err = wk.err;
         a.tol = o->tol;
         a.inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.0;
         a.maxit = o->maxit; a.max_outer = o->max_outer;

@@ -37,7 +37,7 @@ struct PcgArgs {
     double* z;             // n workspace
     double* part_w;        // G x n
     double* part_s;        // G x PART_S
-    unsigned* bar;         // 2 words
+    unsigned long long* bar;  // grid barrier count (zeroed before the launch)
     unsigned* err;
     double tol, inner_tol;
     int32_t maxit, max_outer;
@@ -349,6 +349,7 @@ struct Ring {
     uint64_t* ebars;
     uint32_t qphase, ephase;
     f2* s_q;
+    uint64_t pol;         // L2 policy of the streamed rows (evict first)
 };
 // Stage geometry of a pass: rows per warp (2 when four stages of 2 rows per warp fit),
 // rows per stage R, slots in the ring (>= 3 unless a row is very long).
@@ -377,7 +378,7 @@ __device__ __forceinline__ Geo geometry(int64_t ld, int es, int nwarps, int rbyt
 // thread 0: start the bulk copy of `bytes` at src into slot `slot`
 __device__ __forceinline__ void ring_issue(Ring& ring, int slot, const Geo& g, const char* src, uint32_t bytes) {
     mbar_expect_tx(&ring.bars[slot], bytes);
-    bulk_g2s(ring.buf + slot * g.stage_bytes, src, bytes, &ring.bars[slot]);
+    bulk_g2s_hint(ring.buf + slot * g.stage_bytes, src, bytes, &ring.bars[slot], ring.pol);
 }
 // all threads: wait for slot `slot`, flip its phase bit
 __device__ __forceinline__ bool ring_wait(Ring& ring, int slot) {
@@ -470,7 +471,7 @@ __device__ __forceinline__ bool row_pass_rpw(const PcgArgs& a, const void* vals,
         }
         slot = (slot + 1 == g.slots) ? 0 : slot + 1;
     }
-    if (!ok && threadIdx.x == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    if (!ok && threadIdx.x == 0) raise_grid_error(a.err, a.bar, DEV_ERR_TIMEOUT);
     // cross-warp reduction in a fixed order (the drained ring holds the per-warp vectors)
     RT* s_red = reinterpret_cast<RT*>(ring.buf);
     Ops::store(acc, s_red + (int64_t)wid * NMAX, lane);
@@ -642,7 +643,7 @@ __device__ __forceinline__ bool row_pass_split(const PcgArgs& a, const void* val
         for (int c = 0; c < CPL; ++c)
             if (FULL || col0 + c < n) pw[col0 + c] = df_to_double(df_norm(acc[c]));
     }
-    if (!ok) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    if (!ok) raise_grid_error(a.err, a.bar, DEV_ERR_TIMEOUT);
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -669,12 +670,21 @@ __device__ __forceinline__ bool row_pass(const PcgArgs& a, const void* vals, con
 }
 
 // sum_g part_s[g][slot] over all CTAs, computed by the calling warp (every warp of every
-// CTA sums in the same order, so all agree bit for bit); no block barrier.
+// CTA sums in the same order, so all agree bit for bit); no block barrier.  Four loads per
+// lane are in flight together.
 __device__ __forceinline__ double warp_grid_scalar(const PcgArgs& a, int slot) {
-    const int lane = threadIdx.x & 31;
-    double t = 0.0;
-    for (int g = lane; g < (int)gridDim.x; g += 32) t += a.part_s[(int64_t)g * PART_S + slot];
-    return warp_sum(t);
+    const int lane = threadIdx.x & 31, G = (int)gridDim.x;
+    const double* ps = a.part_s + slot;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int g = lane;
+    for (; g + 96 < G; g += 128) {
+        t0 += ps[(int64_t)g * PART_S];
+        t1 += ps[(int64_t)(g + 32) * PART_S];
+        t2 += ps[(int64_t)(g + 64) * PART_S];
+        t3 += ps[(int64_t)(g + 96) * PART_S];
+    }
+    for (; g < G; g += 32) t0 += ps[(int64_t)g * PART_S];
+    return warp_sum((t0 + t1) + (t2 + t3));
 }
 
 // Writes the CTA partials pa, pb (one per warp, in s_scal) to part_s[cta][slot_a/slot_b].
@@ -718,23 +728,111 @@ __device__ __forceinline__ void op_rows(const PcgArgs& a, int64_t c0, int64_t c1
                                         const double* s_v, double* s_scal) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const OPT* op = reinterpret_cast<const OPT*>(a.op);
+    const int64_t n = a.n;
     double part = 0.0;
     for (int64_t j = c0 + wid; j < c1; j += nwarps) {
-        const OPT* row = op + j * a.n;
-        OPT t0 = OPT(0), t1 = OPT(0);
+        const OPT* row = op + j * n;
+        OPT t0 = OPT(0), t1 = OPT(0), t2 = OPT(0), t3 = OPT(0);
         int64_t k = lane;
-        for (; k + 32 < a.n; k += 64) {
+#pragma unroll 4
+        for (; k + 96 < n; k += 128) {
             t0 = fma(row[k], (OPT)s_v[k], t0);
             t1 = fma(row[k + 32], (OPT)s_v[k + 32], t1);
+            t2 = fma(row[k + 64], (OPT)s_v[k + 64], t2);
+            t3 = fma(row[k + 96], (OPT)s_v[k + 96], t3);
         }
-        if (k < a.n) t0 = fma(row[k], (OPT)s_v[k], t0);
-        double zj = (double)warp_sum(t0 + t1);
+        for (; k < n; k += 32) t0 = fma(row[k], (OPT)s_v[k], t0);
+        const double zj = (double)warp_sum((t0 + t1) + (t2 + t3));
         if (lane == 0) {
             a.z[j] = zj;
             part = fma(s_v[j], zj, part);
         }
     }
     cta_partials(a, part, 0.0, 2, 7, s_scal);
+}
+
+// The phase after the fused pass: p^T w as the grid sum of the CTAs' ||Â p||^2 partials
+// (computed by every warp), then for the owned columns w_j = (1/d_j) sum_g part_w[g][j],
+// y_j += alpha p_j, g_j -= alpha w_j and the CTA's partial of ||g||^2 (slot 1).  The loads
+// of p^T w's partials, of a warp's first column's partials and of its y_j and g_j are all
+// issued before any of them is used.  Returns false on a PCG breakdown (non-positive or
+// non-finite p^T w or rho), the same decision in every thread of the grid.
+__device__ __forceinline__ bool step_update(const PcgArgs& a, int64_t c0, int64_t c1, double rho,
+                                            const double* s_p, const double* s_invd, double* s_scal) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int G = (int)gridDim.x;
+    const int64_t n = a.n;
+    const int64_t j0 = c0 + wid;
+    const bool own = j0 < c1;
+    double yj = 0.0, gj = 0.0;
+    if (own && lane == 0) { yj = a.y[j0]; gj = a.g[j0]; }
+    const double* ps = a.part_s;
+    const double* pw = a.part_w + (own ? j0 : 0);
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+    int g = lane;
+    for (; g + 96 < G; g += 128) {
+        t0 += ps[(int64_t)g * PART_S];
+        t1 += ps[(int64_t)(g + 32) * PART_S];
+        t2 += ps[(int64_t)(g + 64) * PART_S];
+        t3 += ps[(int64_t)(g + 96) * PART_S];
+        if (own) {
+            u0 += pw[(int64_t)g * n];
+            u1 += pw[(int64_t)(g + 32) * n];
+            u2 += pw[(int64_t)(g + 64) * n];
+            u3 += pw[(int64_t)(g + 96) * n];
+        }
+    }
+    for (; g < G; g += 32) {
+        t0 += ps[(int64_t)g * PART_S];
+        if (own) u0 += pw[(int64_t)g * n];
+    }
+    const double pTw = warp_sum((t0 + t1) + (t2 + t3));
+    const double wsum = warp_sum((u0 + u1) + (u2 + u3));
+    if (!(pTw > 0.0) || !(rho > 0.0) || !isfinite(pTw) || !isfinite(rho)) return false;
+    const double alpha = rho / pTw;
+    double part = 0.0;
+    if (own && lane == 0) {
+        const double w = wsum * s_invd[j0];
+        yj = fma(alpha, s_p[j0], yj);
+        gj = fma(-alpha, w, gj);
+        a.y[j0] = yj;
+        a.g[j0] = gj;
+        part = gj * gj;
+    }
+    for (int64_t j = j0 + nwarps; j < c1; j += nwarps) {   // more columns than warps
+        double t = 0.0;
+        for (int gg = lane; gg < G; gg += 32) t += a.part_w[(int64_t)gg * n + j];
+        t = warp_sum(t);
+        if (lane == 0) {
+            const double w = t * s_invd[j];
+            a.y[j] = fma(alpha, s_p[j], a.y[j]);
+            const double gn = fma(-alpha, w, a.g[j]);
+            a.g[j] = gn;
+            part += gn * gn;
+        }
+    }
+    cta_partials(a, part, 0.0, 1, 6, s_scal);
+    return true;
+}
+
+// Copies the n-vector src (global) into s_dst and returns the grid sum of part_s[][slot];
+// the vector's loads and the partials' loads are in flight together.
+template <int NMAX>
+__device__ __forceinline__ double stage_with_scalar(const PcgArgs& a, const double* src, double* s_dst, int slot) {
+    constexpr int PER = (NMAX + 511) / 512;
+    double v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int64_t j = threadIdx.x + (int64_t)r * blockDim.x;
+        v[r] = j < a.n ? src[j] : 0.0;
+    }
+    const double s = warp_grid_scalar(a, slot);
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int64_t j = threadIdx.x + (int64_t)r * blockDim.x;
+        if (j < a.n) s_dst[j] = v[r];
+    }
+    return s;
 }
 
 template <int DT, int DTR, int NMAX, typename OPT>
@@ -749,7 +847,8 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
     const int nwarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31;
     const int RB = ring_bytes(NMAX);
-    Ring ring{smem_raw, s_bars, 0u, RB, nullptr, 0u, 0, s_qbars, s_ebars, 0u, 0u, s_q};
+    Ring ring{smem_raw, s_bars, 0u, RB, nullptr, 0u, 0, s_qbars, s_ebars, 0u, 0u, s_q, l2_evict_first_policy()};
+    unsigned long long bar_epoch = 0;   // grid barriers passed (the same count in every CTA)
     double* s_p = reinterpret_cast<double*>(smem_raw + RB);  // NMAX: p (replicated)
     double* s_v = s_p + NMAX;        // NMAX: D^{-1} x vector for the row pass, or g
     double* s_vc = s_v + NMAX;       // NMAX: s_v in the compute type of the row pass
@@ -774,7 +873,7 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
     const char* mv_src = reinterpret_cast<const char*>(a.vals) + r0 * (int64_t)gmv.row_bytes;
 #define LSQ_BARRIER()                                   \
     do {                                                \
-        if (!grid_barrier(a.bar, G, a.err, a.max_polls)) { \
+        if (!grid_barrier(a.bar, G, a.err, bar_epoch, a.max_polls)) { \
             ring_drain(ring);                           \
             return;                                     \
         }                                               \
@@ -853,34 +952,40 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
                 row_pass<DT, NMAX, PASS_MATVEC>(a, a.vals, s_v, s_vc, s_scal, r0, r1, ring);
                 ring_prefetch(ring, mv_src, gmv, r1 - r0);
                 LSQ_BARRIER();
-                const double pw = warp_grid_scalar(a, 0);
-                if (!(pw > 0.0) || !(rho > 0.0) || !isfinite(pw) || !isfinite(rho)) {
+                if (!step_update(a, c0, c1, rho, s_p, s_invd, s_scal)) {
                     status = LSQ_ERR_BREAKDOWN; broke = true; break;
                 }
-                const double alpha = rho / pw;
-                slice_reduce(a, c0, c1, 1, 6, s_scal, s_invd, [&](int64_t j, double w) {
-                    a.y[j] = fma(alpha, s_p[j], a.y[j]);
-                    double gj = fma(-alpha, w, a.g[j]);
-                    a.g[j] = gj;
-                    return make_double2(gj * gj, 0.0); });
                 LSQ_BARRIER();
                 ++iters;
                 dirty = true;
-                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.g[j];
-                gg = warp_grid_scalar(a, 1);
+                gg = stage_with_scalar<NMAX>(a, a.g, s_v, 1);
                 rec = sqrt(gg) / hn;
                 __syncthreads();
                 if (rec <= a.tol || sqrt(gg) <= a.inner_tol * gstart) break;
                 if (iters >= a.maxit) break;
                 op_rows<OPT>(a, c0, c1, s_v, s_scal);
                 LSQ_BARRIER();
-                const double rho_new = warp_grid_scalar(a, 2);
-                const double beta = rho_new / rho;
-                rho = rho_new;
-                for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-                    const double pj = fma(beta, s_p[j], a.z[j]);
-                    s_p[j] = pj;
-                    s_v[j] = pj * s_invd[j];
+                {
+                    // rho' = g^T z over the grid and p = z + beta p; z's loads go out first
+                    constexpr int PER = (NMAX + 511) / 512;
+                    double zv[PER];
+#pragma unroll
+                    for (int r = 0; r < PER; ++r) {
+                        const int64_t j = threadIdx.x + (int64_t)r * blockDim.x;
+                        zv[r] = j < n ? a.z[j] : 0.0;
+                    }
+                    const double rho_new = warp_grid_scalar(a, 2);
+                    const double beta = rho_new / rho;
+                    rho = rho_new;
+#pragma unroll
+                    for (int r = 0; r < PER; ++r) {
+                        const int64_t j = threadIdx.x + (int64_t)r * blockDim.x;
+                        if (j < n) {
+                            const double pj = fma(beta, s_p[j], zv[r]);
+                            s_p[j] = pj;
+                            s_v[j] = pj * s_invd[j];
+                        }
+                    }
                 }
                 __syncthreads();
             }

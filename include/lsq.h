@@ -231,8 +231,9 @@ LSQ_API lsq_status lsq_precond_apply(const lsq_precond* P, const double* r, doub
  * residual Â^T (b - Â y) is recomputed (in FP64 from vals_f64 when given); if it misses
  * the tolerance PCG restarts from y (one outer step), up to o->max_outer times.
  *
- * Dense A (values F64, F32 or F32X2; BF16 returns LSQ_ERR_UNSUPPORTED): the whole loop of
- * each column runs inside one persistent cooperative kernel.  CSR A (values F64, F32,
+ * Dense A (values F64, F32, BF16 or F32X2): the whole loop of each column runs inside one
+ * persistent cooperative kernel.  FP32 and BF16 values are products and sums in FP32 (BF16
+ * widened exactly on load), F32X2 in double-float, with FP64 restarts from vals_f64.  CSR A (values F64, F32,
  * BF16 or F32X2; P built with sweeps <= 32): each iteration is a row pass, a column pass
  * and the level-ordered sweeps of Alg. 3; k >= 2 columns advance together in blocks of up
  * to 32, with one pass over A and one sweep per iteration for the whole block.

@@ -53,10 +53,6 @@ static lsq_status check_dense_solve(const lsq_matrix* A, const lsq_precond* P, i
         set_error("sparse PCG is not available in this build");
         return LSQ_ERR_UNSUPPORTED;
     }
-    if (A->dtype == LSQ_BF16) {
-        set_error("dense PCG supports F64, F32 and F32X2 values in this build");
-        return LSQ_ERR_UNSUPPORTED;
-    }
     const size_t es = elem_size(A->dtype);
     LSQ_CHECK_ARG(aligned16(A->vals), "A->vals must be 16-byte aligned");
     LSQ_CHECK_ARG(((size_t)A->ld * es) % 16 == 0, "A->ld * element size must be a multiple of 16 bytes");
@@ -71,7 +67,7 @@ static lsq_status check_dense_solve(const lsq_matrix* A, const lsq_precond* P, i
     *dtr = (A->dtype == LSQ_F64 || A->vals_f64) ? LSQ_F64 : A->dtype;
     *nmax = pick_nmax(*dt, *dtr, A->n);
     if (*nmax == 0) {
-        set_error("dense PCG supports n <= 1024 with FP64 values or residuals, n <= 2048 otherwise");
+        set_error("dense PCG supports n <= 2048 with FP32 values and residuals, n <= 1024 otherwise");
         return LSQ_ERR_UNSUPPORTED;
     }
     return LSQ_OK;
@@ -117,6 +113,7 @@ static lsq_status solve_columns(const lsq_matrix* A, const lsq_precond* P, const
         int G = 0;
         lsq_status ls = dt == LSQ_F64 ? launch_pcg_f64(nmax, P->op_dtype, a, o->grid_ctas, st, &G)
                       : dt == LSQ_F32 ? launch_pcg_f32(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G)
+                      : dt == LSQ_BF16 ? launch_pcg_bf16(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G)
                                       : launch_pcg_f32x2(nmax, dtr, P->op_dtype, a, o->grid_ctas, st, &G);
         if (ls != LSQ_OK) return ls;
         LSQ_CUDA(cudaGetLastError());
@@ -289,6 +286,8 @@ extern "C" lsq_status lsq_pcg_adjoint(const lsq_matrix* A, const lsq_precond* P,
         return adjoint_dense<LSQ_F64>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
     if (A->dtype == LSQ_F32X2)
         return adjoint_dense<LSQ_F32X2>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
+    if (A->dtype == LSQ_BF16)
+        return adjoint_dense<LSQ_BF16>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
     return adjoint_dense<LSQ_F32>(A, P, X, B, G, k, ldb, ldx, grad_b, grad_vals, Lambda, o, info, st);
 }
 

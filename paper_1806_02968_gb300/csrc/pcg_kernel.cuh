@@ -238,6 +238,109 @@ template <int NMAX> struct RowOps<LSQ_F32, NMAX> {
     static __device__ __forceinline__ double q_out(const Q& q) { return df_to_double(q.s); }
 };
 
+// BF16 values: a lane reads 8 values (16 bytes) per chunk and widens them exactly to FP32;
+// products and sums as in the FP32 form (FP32 row dots and column accumulators, sum of
+// q_i^2 in double-float).  The stored matrix is half the bytes of FP32.
+__device__ __forceinline__ void bf16x8_to_f32(uint4 u, float (&f)[8]) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        f[2 * i] = __uint_as_float(w[i] << 16);            // element 2i (low half)
+        f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u); // element 2i + 1 (high half)
+    }
+}
+template <int NMAX> struct RowOps<LSQ_BF16, NMAX> {
+    static constexpr int ES = 2, VEC = 8, NCH = (NMAX + 32 * 8 - 1) / (32 * 8);
+    typedef float VT;
+    typedef float RT;
+    struct Acc { float v[NCH][VEC]; };
+    struct Q { f2 s; };
+    static __device__ __forceinline__ void zero(Acc& a, Q& q) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) a.v[c][v] = 0.f;
+        q.s = f2{0.f, 0.f};
+    }
+    static __device__ __forceinline__ VT stage(double x) { return (float)x; }
+    // the 8 values of chunk c of a row, zero beyond n (row padding)
+    static __device__ __forceinline__ void load8(const char* rp, int col, int64_t n, float (&f)[8]) {
+        bf16x8_to_f32(*reinterpret_cast<const uint4*>(rp + 2 * col), f);
+        if (col + 8 > n) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) if (col + i >= n) f[i] = 0.f;
+        }
+    }
+    template <int MODE, bool TWO>
+    static __device__ __forceinline__ void row(const char* rp0, const char* rp1, bool has1,
+                                               const VT* sv, int lane, int64_t n, double b0,
+                                               double b1, Acc& A, Q& Qa) {
+        float q0, q1 = 0.f;
+        if (MODE == PASS_RHS) {
+            q0 = (float)b0; q1 = (float)b1;
+        } else {
+            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int col = c * 32 * VEC + lane * VEC;
+                if (col < n) {
+                    const float4 s0 = *reinterpret_cast<const float4*>(sv + col);
+                    const float4 s1 = *reinterpret_cast<const float4*>(sv + col + 4);
+                    const float sx[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+                    float v[8];
+                    load8(rp0, col, n, v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) d0[i & 3] = fmaf(v[i], sx[i], d0[i & 3]);
+                    if (TWO) {
+                        float w[8];
+                        load8(rp1, col, n, w);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) d1[i & 3] = fmaf(w[i], sx[i], d1[i & 3]);
+                    }
+                }
+            }
+            float d0s = (d0[0] + d0[1]) + (d0[2] + d0[3]), d1s = (d1[0] + d1[1]) + (d1[2] + d1[3]);
+            if (TWO) pair_reduce2<float>(d0s, d1s, lane, [](float& x, float y) { x += y; }, shfl_f, bcast_f);
+            else d0s = warp_sum(d0s);
+            if (MODE == PASS_MATVEC) { q0 = d0s; q1 = d1s; }
+            else { q0 = (float)(b0 - (double)d0s); q1 = (float)(b1 - (double)d1s); }
+        }
+        if (!has1) q1 = 0.f;
+        df_add_sq(Qa.s, q0);
+        if (TWO) df_add_sq(Qa.s, q1);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            if (col < n) {
+                float v[8];
+                load8(rp0, col, n, v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) A.v[c][i] = fmaf(q0, v[i], A.v[c][i]);
+                if (TWO) {
+                    float w[8];
+                    load8(rp1, col, n, w);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) A.v[c][i] = fmaf(q1, w[i], A.v[c][i]);
+                }
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(const Acc& A, RT* dst, int lane) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = c * 32 * VEC + lane * VEC;
+            if (col < NMAX) {
+                *reinterpret_cast<float4*>(dst + col) = make_float4(A.v[c][0], A.v[c][1], A.v[c][2], A.v[c][3]);
+                *reinterpret_cast<float4*>(dst + col + 4) = make_float4(A.v[c][4], A.v[c][5], A.v[c][6], A.v[c][7]);
+            }
+        }
+    }
+    static __device__ __forceinline__ void red_add(RT& acc, RT v) { acc += v; }
+    static __device__ __forceinline__ RT red_zero() { return 0.f; }
+    static __device__ __forceinline__ double red_out(RT v) { return (double)v; }
+    static __device__ __forceinline__ double q_out(const Q& q) { return df_to_double(q.s); }
+};
+
 template <int NMAX> struct RowOps<LSQ_F32X2, NMAX> {
     static constexpr int ES = 8, VEC = 2, NCH = NMAX / (32 * VEC);
     typedef f2 VT;

@@ -39,5 +39,6 @@ inline int pcg_max_grid() {
 lsq_status launch_pcg_f64(int64_t nmax, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
 lsq_status launch_pcg_f32(int64_t nmax, int dtr, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
 lsq_status launch_pcg_f32x2(int64_t nmax, int dtr, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
+lsq_status launch_pcg_bf16(int64_t nmax, int dtr, int opt_dtype, PcgArgs& a, int cap, cudaStream_t st, int* G);
 
 }  // namespace lsq

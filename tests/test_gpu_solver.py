@@ -171,6 +171,32 @@ def test_pcg_f32_values_with_f64_refinement(lsq, orc):
     assert info.outer[0] >= 1
 
 
+@pytest.mark.parametrize("shape", [(16384, 128, 0), (6001, 100, 4)])
+def test_pcg_bf16_values_with_f64_refinement(lsq, orc, shape):
+    """BF16 dense values (a variant of the precision form): the inner iteration reads the
+    values in BF16 (half the bytes of FP32) and computes in FP32; restarts use the FP64 copy
+    of the same values.  The oracle gets the BF16-rounded matrix, so the result must be the
+    FP64 solution of that matrix.  (6001, 100, 4): ragged m, n and a padded leading
+    dimension (a multiple of 8 BF16 values)."""
+    m, n, pad = shape
+    mat = W.gaussian_dense(m, n, 31)
+    Mx, keep, seen = to_device(lsq, mat, "bf16", with_f64=True, ld_pad=pad)
+    o = lsq.opts(seed=31, precond_dtype=1, max_outer=30, inner_tol=1e-4)
+    idx, p, d = lsq.lsq_sample_rows(Mx, o)
+    P = lsq.lsq_build_precond(Mx, idx, p, d, o)
+    smp = orc.Sample(seen, seed=31)
+    assert np.array_equal(idx.cpu().numpy(), smp.idx)
+    Mo = orc.SampledM(smp)
+    xs, b = W.rhs_for(seen, 2, 1e-3, 38)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    kappa = np.linalg.cond(seen["A"] / smp.d)
+    for c in range(2):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+        assert info.converged[c] == 1 and info.relres_true[c] <= o.tol and info.outer[c] >= 1
+        assert_solution(X[c], y / smp.d, kappa, f"bf16 dense {m}x{n} column {c}")
+
+
 def test_pcg_deterministic(lsq, orc):
     mat = W.gaussian_dense(4096, 128, 1001)
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1001)

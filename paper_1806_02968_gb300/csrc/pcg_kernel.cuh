@@ -723,6 +723,11 @@ __device__ __forceinline__ bool row_pass_split(const PcgArgs& a, const void* val
                         }
                     }
                 }
+                // renormalise once per stage: the low word then collects the errors of at most
+                // 16 products, so the cascade's second-order error grows with the number of
+                // stages, not with the square of the number of rows a lane sums
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) acc[c] = df_norm(acc[c]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.ebars[slot]);

@@ -28,15 +28,6 @@ def _setup(lsq, orc, mat, seed):
     return Mx, keep, seen, o, P, smp, orc.SampledM(smp)
 
 
-@pytest.fixture
-def tiny_waits(lsq):
-    lsq.set_wait_limit(2)
-    try:
-        yield
-    finally:
-        lsq.set_wait_limit(0)
-
-
 def test_sparse_sweep_wait_timeout_then_recovers(lsq, orc):
     """The sweeps of a graph incidence matrix with wide levels run on the whole grid, each
     row waiting for the values it depends on: with 2 polls per wait those waits run out."""
@@ -63,13 +54,39 @@ def test_sparse_sweep_wait_timeout_then_recovers(lsq, orc):
     assert abs(int(info.iters[0]) - oi["iters"]) <= 2
 
 
-def test_sparse_block_sweep_wait_timeout(lsq, orc, tiny_waits):
+def test_sparse_block_sweep_wait_timeout(lsq, orc):
     """The same for a block of right-hand sides (the block sweep forms)."""
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, W.graph_incidence(20000, 90000, 4), 1003)
     xs, b = W.rhs_for(seen, 4, 1e-4, 17)
-    with pytest.raises(lsq.L.LsqError) as e:
-        lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
-    assert e.value.code == TIMEOUT
+    B = torch.from_numpy(b).cuda()
+    lsq.set_wait_limit(2)
+    try:
+        with pytest.raises(lsq.L.LsqError) as e:
+            lsq.lsq_pcg_solve(Mx, P, B, o)
+        assert e.value.code == TIMEOUT
+    finally:
+        lsq.set_wait_limit(0)
+    X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    assert info.status == 0 and all(info.converged == 1)
+
+
+def test_level_builder_wait_timeout(lsq, orc):
+    """Building the sparse handle computes the level schedules with dependency waits too."""
+    Mx, keep, seen = to_device(lsq, W.graph_incidence(20000, 90000, 4))
+    o = lsq.opts(seed=1003)
+    idx, p, d = lsq.lsq_sample_rows(Mx, o)
+    lsq.set_wait_limit(2)
+    try:
+        with pytest.raises(lsq.L.LsqError) as e:
+            lsq.lsq_build_precond(Mx, idx, p, d, o)
+        assert e.value.code == TIMEOUT
+    finally:
+        lsq.set_wait_limit(0)
+    P = lsq.lsq_build_precond(Mx, idx, p, d, o)
+    smp = orc.Sample(seen, seed=1003)
+    Mo = orc.SampledM(smp)
+    rp, ci, va = (t.cpu().numpy() for t in P.M_csr())
+    assert np.array_equal(rp, Mo.row_ptr) and np.array_equal(ci, Mo.col)
 
 
 def test_dense_grid_barrier_timeout_then_recovers(lsq, orc):

@@ -255,3 +255,31 @@ def test_sparse_cg_baseline_matches_oracle(lsq, orc, k):
         assert_iterations(info.iters[c], oi["iters"], _variants(orc, seen, smp, Mo, b[c], o), f"CG sprand k={k} column {c}")
     r = torch.from_numpy(np.random.default_rng(0).standard_normal((2, seen["n"]))).cuda()
     assert torch.equal(P.apply(r), r)
+
+
+def test_sparse_block_solve_captured_in_a_cuda_graph(lsq, orc):
+    """A block of 32 right-hand sides (graph incidence, FP64) runs as one persistent launch
+    plus its setup kernels, with no host synchronisation: lsq_pcg_solve is captured into a
+    CUDA graph, and every replay writes the bits of the direct call."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES["graph"](), 1003)
+    xs, b = W.rhs_for(seen, 32, 1e-4, 99)
+    B = torch.from_numpy(b).cuda()
+    X0, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    assert all(info.converged == 1)
+    X = torch.zeros_like(X0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    n0 = lsq.launches()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            lsq.lsq_pcg_solve(Mx, P, B, o, X=X, stream=s)
+    assert 1 <= lsq.launches() - n0 <= 4       # the persistent kernel and its setup kernels
+    for _ in range(2):
+        X.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(X, X0)
+    # one column against the oracle, for good measure
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[5], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+    assert_solution(X[5].cpu().numpy(), y / smp.d, np.linalg.cond(W.dense_from_csr(seen) / smp.d), "captured")

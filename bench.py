@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
-    ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch"], default="udv",
+    ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch", "tc", "sampling"],
+                    default="udv",
                     help="udv: the timed benchmark; the others measure one other configuration alone")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations and the FP64 comparison solve after the timed region")
@@ -765,12 +766,129 @@ def run_batch_workload(args):
           flush=True)
 
 
+def tc_grid(steps=3, warmup=1):
+    """Sweeps t in {1, 2, 5} (and t = 0, CG on the normalised A) against the sample factor
+    C in {2, 4, 8} (s = ceil(C n ln n)): iterations and time to 1e-10 of a whole solve
+    (sampling, preconditioner, PCG) on a Gaussian 4096 x 128, a UDV 20000 x 256 with
+    kappa(A) = 1e3 and a sparse random 100000 x 2000 (8 per row), FP64, one right-hand side
+    b = A x* + 1e-3 N(0,1).  Each setting is timed over `steps` solves after `warmup`."""
+    import torch
+    import workloads as W
+    from paper_1806_02968_gb300 import api
+    mats = {"gaussian_dense_4096x128": W.gaussian_dense(4096, 128, 7),
+            "udv_dense_20000x256_kappa1e3": W.udv_dense(20000, 256, 1e3, 7),
+            "sparse_random_100000x2000_8nnz": W.sparse_random(100000, 2000, 8, 7)}
+    out = {}
+    for name, mat in mats.items():
+        xs, b = W.rhs_for(mat, 1, 1e-3, 8)
+        if mat["kind"] == "dense":
+            A = torch.from_numpy(mat["A"]).cuda()
+            Mx, keep = api.Matrix(A), [A]
+        else:
+            keep = [torch.from_numpy(mat[k]).cuda() for k in ("row_ptr", "col_idx", "vals")]
+            Mx = api.Matrix(row_ptr=keep[0], col_idx=keep[1], vals=keep[2], n=mat["n"])
+        B = torch.from_numpy(b[0]).cuda()
+        rows = {}
+        for t in (0, 1, 2, 5):
+            for C in (2.0, 4.0, 8.0):
+                if t == 0 and C != 4.0:
+                    continue      # CG does not sample
+                o = api.opts(seed=11, sweeps=t, sample_factor=C)
+                times = []
+                for rep in range(warmup + steps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    idx, p, d = api.lsq_sample_rows(Mx, o)
+                    P = api.lsq_build_precond(Mx, idx, p, d, o)
+                    x, info = api.lsq_pcg_solve(Mx, P, B, o)
+                    torch.cuda.synchronize()
+                    if rep >= warmup:
+                        times.append(time.perf_counter() - t0)
+                rows[f"t={t},C={C:g}"] = {"iters": int(info.iters[0]), "ms": 1e3 * float(np.mean(times)),
+                                          "relres_true": float(info.relres_true[0]), "s": int(info.s)}
+        out[name] = rows
+    return out
+
+
+def sampling_cmp(steps=3, warmup=1):
+    """The method's row density (squared norms, Eq. R2P) against uniform sampling (the
+    comparison of Sec. 3.1) and against CG on the normalised A, on matrices whose rows differ:
+    400 heavy Gaussian rows among 20000 (the rest scaled by 1e-3), the sparse random
+    4,000,000 x 40,000 configuration (per-row scales 10^U(-2, 2); FP32 values, FP64 restarts),
+    and the semi-Gaussian [B 0; 0 I] of Sec. 5.2 (coherent, but its identity block is already
+    its own normal matrix).  Iterations and time to 1e-10 of a whole solve."""
+    import torch
+    import workloads as W
+    from paper_1806_02968_gb300 import api
+    rng = np.random.default_rng(4)
+    heavy = rng.standard_normal((20000, 100))
+    heavy[400:] *= 1e-3
+    mats = {"heavy_rows_dense_20000x100": ({"kind": "dense", "A": heavy}, "f64"),
+            "sparse_random_4000000x40000_8nnz": (sparse_matrix("sparse"), "f32"),
+            "semi_gaussian_dense_10000x200": (W.semi_gaussian_dense(10000, 200, 21), "f64")}
+    out = {}
+    for name, (mat, dt) in mats.items():
+        xs, b = W.rhs_for(mat, 1, 1e-3, 6)
+        if mat["kind"] == "dense":
+            A = torch.from_numpy(mat["A"]).cuda()
+            Mx, keep, pdt = api.Matrix(A), [A], 0
+        else:
+            keep = [torch.from_numpy(mat[k]).cuda() for k in ("row_ptr", "col_idx", "vals")]
+            v = keep[2].float() if dt == "f32" else keep[2]
+            keep.append(v)
+            Mx = api.Matrix(row_ptr=keep[0], col_idx=keep[1], vals=v, n=mat["n"],
+                            vals_f64=keep[2] if dt == "f32" else None)
+            pdt = 1 if dt == "f32" else 0
+        B = torch.from_numpy(b[0]).cuda()
+        rows = {}
+        for label, sampling, sweeps in (("norm2", 0, 1), ("uniform", 1, 1), ("cg", 0, 0)):
+            o = api.opts(seed=5, sweeps=sweeps, sampling=sampling, precond_dtype=pdt, max_outer=50)
+            times = []
+            for rep in range(warmup + steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                idx, p, d = api.lsq_sample_rows(Mx, o)
+                P = api.lsq_build_precond(Mx, idx, p, d, o)
+                x, info = api.lsq_pcg_solve(Mx, P, B, o)
+                torch.cuda.synchronize()
+                if rep >= warmup:
+                    times.append(time.perf_counter() - t0)
+            rows[label] = {"iters": int(info.iters[0]), "ms": 1e3 * float(np.mean(times)),
+                           "relres_true": float(info.relres_true[0]), "unsampled_columns": int(info.n_fixed_diag)}
+        out[name] = rows
+    return out
+
+
+def run_sampling(args):
+    import torch
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"metric": METRIC, "unit": "ms per solve (sampling + preconditioner + PCG)",
+                      "n_gpus": 1, "data": "synthetic", "tol": 1e-10,
+                      "comparison": sampling_cmp(args.steps, args.warmup)}), flush=True)
+
+
+def run_tc(args):
+    import torch
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"metric": METRIC, "unit": "ms per solve (sampling + preconditioner + PCG)",
+                      "n_gpus": 1, "data": "synthetic", "dtype": "f64", "tol": 1e-10,
+                      "grid": tc_grid(args.steps, args.warmup)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch_workload(args)
+    elif args.workload == "tc":
+        run_tc(args)
+    elif args.workload == "sampling":
+        run_sampling(args)
     elif args.workload not in ("udv", "gauss"):
         run_sparse_workload(args)
     else:

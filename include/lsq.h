@@ -95,6 +95,9 @@ typedef struct {
     double inner_tol;      /* refinement form only: relative tolerance of each inner
                               solve; 0 = tol (no separate inner tolerance) */
     int32_t grid_ctas;     /* 0 = one persistent CTA per SM (x occupancy); else a cap */
+    int32_t sampling;      /* row sampling density of Alg. 1: 0 = p_i proportional to the squared
+                              row norm (Eq. R2P, the method); 1 = uniform p_i = 1/m (the
+                              comparison of Sec. 3.1, which coherent matrices defeat); 0 */
 } lsq_opts;
 
 /* Per-right-hand-side results, written to caller-owned HOST arrays of length k (any
@@ -136,7 +139,9 @@ LSQ_API int64_t lsq_sample_size(int64_t n, double C);
  *   draw t: Philox4x64-10 with key (seed, 0x5A4D504C), counter (t,0,0,0) -> words
  *   (r0, r1, ...); U = r1 2^64 + r0; i_t = max{i : sum_{l<i} w_l <= floor(U W / 2^128)}.
  * A column with c_j = 0 keeps d_j = 1 and no sampling weight.  max a_ij^2 must lie in
- * [2^-900, 2^900] and every value must be finite (else LSQ_ERR_INVALID).
+ * [2^-900, 2^900] and every value must be finite (else LSQ_ERR_INVALID).  With
+ * o->sampling == 1 every row has weight w_i = 1 (p_i = 1/m; the column scales are still
+ * computed), so the same draws give i_t = floor(U m / 2^128).
  *
  *   A          matrix (device arrays), any dtype
  *   o          options (normalize, seed, sample_factor); host

@@ -162,13 +162,24 @@ def u128(lo, hi):
 
 
 class Sample:
-    """Everything Alg. 1 + Alg. 2 steps 1-2 produce for one matrix and seed."""
+    """Everything Alg. 1 + Alg. 2 steps 1-2 produce for one matrix and seed.
+
+    sampling="norm2" is the method's density, p_i proportional to the squared norm of the
+    normalised row (Eq. R2P).  sampling="uniform" is the comparison of Sec. 3.1: every row
+    has the same weight (w_i = 1, p_i = 1/m); the column scales of Alg. 2 step 1 are still
+    computed, and the draws and the scaling 1/(s p_i) go through the same steps."""
 
     def __init__(self, mat, seed: int, s: int | None = None, normalize: bool = True,
-                 C_factor: float = 4.0):
+                 C_factor: float = 4.0, sampling: str = "norm2"):
         self.mat = as_mat(mat)
         self.d2, self.d, self.inv_d2, self.E1 = col_scales(self.mat, normalize)
-        self.w_lo, self.w_hi = row_weights(self.mat, self.inv_d2)
+        if sampling == "uniform":
+            self.w_lo = np.ones(self.mat.m, np.uint64)
+            self.w_hi = np.zeros(self.mat.m, np.uint64)
+        elif sampling == "norm2":
+            self.w_lo, self.w_hi = row_weights(self.mat, self.inv_d2)
+        else:
+            raise ValueError(sampling)
         self.P_lo, self.P_hi = prefix(self.w_lo, self.w_hi)
         self.s = sample_size(self.mat.n, C_factor) if not s else int(s)
         self.seed = seed

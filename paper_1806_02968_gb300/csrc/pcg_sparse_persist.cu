@@ -38,6 +38,7 @@ struct BkPersist {
     int res64;                // true residuals from FP64 values
     int smode;                // sweep form: 0 lane per column, 1 lane per entry, 2 CTA per row
     int max_outer;
+    unsigned bar_polls;       // bound of every grid-barrier wait
 };
 
 __device__ __forceinline__ unsigned bk_ld_volatile_u32(const unsigned* p) {
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(BK_T, 2) k_bk_persist(BkPersist P) {
 
 #define BK_BAR()                                                              \
     do {                                                                      \
-        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) \
+        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) \
             return;                                                           \
     } while (0)
 
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(BK_T, 2) k_bk_persist(BkPersist P) {
     // norms of x over the grid -> s_gn / s_gnraw (every CTA)
     auto norms = [&](const double* x) -> bool {
         bk_norms_body(a, x, P.n2);
-        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
         if (tid < K) {
             s_gn[tid] = sqrt(__ldcg(P.n2 + tid));
             s_gnraw[tid] = sqrt(__ldcg(P.n2 + BK_MAX + tid));
@@ -121,19 +122,19 @@ __global__ void __launch_bounds__(BK_T, 2) k_bk_persist(BkPersist P) {
     // g = Â^T (b - Â y) (or h - Â^T Â y) and its norms
     auto true_residual = [&]() -> bool {
         for (int64_t t = gtid; t < nK; t += gstride) P.tmpv[t] = a.y[t] * a.inv_d[t / K];
-        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
         if (P.use_h) {
             rows(0, 1, P.tmpv);
-            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             cols(1, a.w);
-            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             for (int64_t t = gtid; t < nK; t += gstride) a.g[t] = a.h[t] - a.w[t];
         } else {
             rows(2, 1, P.tmpv);
-            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             cols(1, a.g);
         }
-        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+        if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
         if (tid < K) s_dirty[tid] = 0;
         return norms(a.g);
     };
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(BK_T, 2) k_bk_persist(BkPersist P) {
     auto precond = [&](bool prefilled) -> bool {
         if (a.sweeps == 0) {   // the comparison method: P = I
             for (int64_t t = gtid; t < nK; t += gstride) a.z[t] = a.g[t];
-            return true;
+            // g^T z next reads z in another thread mapping
+            return grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls);
         }
         const double* eold = nullptr;
         double* bufs[2] = {a.e0, a.e1};
@@ -152,10 +154,10 @@ __global__ void __launch_bounds__(BK_T, 2) k_bk_persist(BkPersist P) {
         for (int t = 0; t < a.sweeps; ++t, ++idx) {
             if (!pre) {
                 fill_empty(bufs[cur]);
-                if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+                if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             }
             sweep(true, eold, bufs[cur], 0, idx);
-            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             if (bk_ld_volatile_u32(&a.S->err) != 0u) return false;
             eold = bufs[cur];
             cur ^= 1;
@@ -164,10 +166,10 @@ __global__ void __launch_bounds__(BK_T, 2) k_bk_persist(BkPersist P) {
             double* dst = (t == a.sweeps - 1) ? a.z : bufs[cur];
             if (!pre) {
                 fill_empty(dst);
-                if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+                if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             }
             sweep(false, eold, dst, (a.sweeps == 1) ? 1 : 0, idx);
-            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, a.max_polls)) return false;
+            if (!grid_barrier(P.bar, gridDim.x, &a.S->err, epoch, P.bar_polls)) return false;
             if (bk_ld_volatile_u32(&a.S->err) != 0u) return false;
             eold = dst;
             cur ^= 1;
@@ -323,6 +325,7 @@ lsq_status bk_persist_launch(int dt, int mt_f32, const BkArgs& a, unsigned long 
     P.a = a;
     P.bar = bar; P.n2 = n2; P.tmpv = tmpv; P.X = X; P.ldx = ldx; P.out = out;
     P.use_h = use_h; P.res64 = res64; P.smode = smode; P.max_outer = max_outer;
+    P.bar_polls = barrier_wait_polls();
     void* params[] = {&P};
     LSQ_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BK_T), params, 0, st));
     count_launch();

@@ -188,11 +188,15 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
 }
 
 template <int DT>
-__global__ void k_rowweight(lsq_matrix A, const double* inv_d2, u128* w) {
+__global__ void k_rowweight(lsq_matrix A, const double* inv_d2, u128* w, int uniform) {
     int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < A.m; i += nwarps) {
+        if (uniform) {   // the uniform density of the comparison in Sec. 3.1: w_i = 1
+            if (lane == 0) w[i] = 1;
+            continue;
+        }
         u128 acc = 0;
         if (A.dense) {
             for (int64_t j = lane; j < A.n; j += 32) {
@@ -415,7 +419,7 @@ static lsq_status sample_launch(const lsq_matrix* A, const lsq_opts* o, int64_t 
     if (A->dense) k_colsum_dense<DT><<<(int)((m + rpb - 1) / rpb), 256, 0, st>>>(Av, E1j, c, rpb);
     else k_colsum_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, E1j, c);
     k_colscale<<<grid_for(n, 256), 256, 0, st>>>(n, o->normalize ? 1 : 0, E1j, E1g, c, d2, inv, d);
-    k_rowweight<DT><<<grid_for(m * 32, 256), 256, 0, st>>>(Av, inv, w);
+    k_rowweight<DT><<<grid_for(m * 32, 256), 256, 0, st>>>(Av, inv, w, o->sampling == 1 ? 1 : 0);
     k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts);
     k_scan_sums<<<1, 1024, 0, st>>>(ts, ntiles);
     k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts, P);
@@ -487,6 +491,7 @@ extern "C" void lsq_default_opts(lsq_opts* o) {
     o->seed = 0;
     o->inner_tol = 0.0;
     o->grid_ctas = 0;
+    o->sampling = 0;
 }
 
 extern "C" lsq_status lsq_set_wait_limit(int64_t max_polls) {
@@ -508,6 +513,7 @@ extern "C" lsq_status lsq_sample_rows(const lsq_matrix* A, const lsq_opts* o, in
     LSQ_CHECK_ARG(o != nullptr, "opts is NULL");
     LSQ_CHECK_ARG(idx_out != nullptr, "idx_out is NULL");
     LSQ_CHECK_ARG(s >= 0, "s < 0");
+    LSQ_CHECK_ARG(o->sampling == 0 || o->sampling == 1, "sampling must be 0 (norm squared) or 1 (uniform)");
     if (s == 0) s = lsq_sample_size(A->n, o->sample_factor);
     LSQ_CHECK_ARG(s > 0 && s < (int64_t)1 << 40, "sample size out of range");
     if (s_out) *s_out = s;
@@ -530,6 +536,7 @@ extern "C" lsq_status lsq_sample_rows_static(const lsq_matrix* A, const lsq_opts
     LSQ_CHECK_ARG(o != nullptr, "opts is NULL");
     LSQ_CHECK_ARG(idx_out != nullptr, "idx_out is NULL");
     LSQ_CHECK_ARG(s >= 0, "s < 0");
+    LSQ_CHECK_ARG(o->sampling == 0 || o->sampling == 1, "sampling must be 0 (norm squared) or 1 (uniform)");
     if (A->m > STATIC_MAX_ROWS || A->n > STATIC_MAX_COLS) {
         set_error("lsq_sample_rows_static: A has more than 262144 rows or 4096 columns, the size of "
                   "its fixed scratch; use lsq_sample_rows");

@@ -9,11 +9,11 @@ from helpers import to_device
 pytestmark = pytest.mark.gpu
 
 
-def _check(lsq, orc, mat, dtype="f64", seed=1, s=0, normalize=True, ld_pad=0):
+def _check(lsq, orc, mat, dtype="f64", seed=1, s=0, normalize=True, ld_pad=0, sampling="norm2"):
     Mx, keep, seen = to_device(lsq, mat, dtype, ld_pad=ld_pad)
-    o = lsq.opts(seed=seed, normalize=int(normalize))
+    o = lsq.opts(seed=seed, normalize=int(normalize), sampling=1 if sampling == "uniform" else 0)
     idx, p, d = lsq.lsq_sample_rows(Mx, o, s=s)
-    smp = orc.Sample(seen, seed=seed, s=s or None, normalize=normalize)
+    smp = orc.Sample(seen, seed=seed, s=s or None, normalize=normalize, sampling=sampling)
     gi = idx.cpu().numpy()
     assert gi.shape == smp.idx.shape
     assert np.array_equal(gi, smp.idx), f"first mismatch at {np.nonzero(gi != smp.idx)[0][:5]}"
@@ -59,6 +59,15 @@ def test_csr_bitexact(lsq, orc):
 def test_coherent_matrix_draws_identity_rows(lsq, orc):
     smp = _check(lsq, orc, W.coherent_dense(5000, 16), seed=3, s=20000)
     assert smp.idx.max() < 16
+
+
+def test_uniform_sampling_bitexact(lsq, orc):
+    """The uniform density of the comparison in Sec. 3.1 (p_i = 1/m): dense, CSR, and the
+    coherent matrix, where most draws land on zero rows."""
+    _check(lsq, orc, W.gaussian_dense(3001, 40, 8), seed=12, sampling="uniform")
+    _check(lsq, orc, W.sparse_random(20000, 300, 8, 3), seed=13, sampling="uniform")
+    smp = _check(lsq, orc, W.coherent_dense(5000, 16), seed=3, s=20000, sampling="uniform")
+    assert (smp.idx >= 16).mean() > 0.99
 
 
 def test_udv_full_size_bitexact(lsq, orc):

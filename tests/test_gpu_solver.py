@@ -197,6 +197,46 @@ def test_pcg_bf16_values_with_f64_refinement(lsq, orc, shape):
         assert_solution(X[c], y / smp.d, kappa, f"bf16 dense {m}x{n} column {c}")
 
 
+def _heavy_rows(m=20000, n=100, heavy=400, seed=4):
+    """Gaussian rows, all but the first `heavy` scaled by 1e-3: a few rows carry the columns."""
+    A = np.random.default_rng(seed).standard_normal((m, n))
+    A[heavy:] *= 1e-3
+    return {"kind": "dense", "A": A}
+
+
+@pytest.mark.parametrize("sampling", ["norm2", "uniform"])
+@pytest.mark.parametrize("case", ["heavy_rows", "sprand"])
+def test_pcg_norm2_against_uniform_sampling(lsq, orc, case, sampling):
+    """The method's density (p_i proportional to the squared row norm, Eq. R2P) against the
+    uniform density of the comparison in Sec. 3.1, on matrices whose row norms vary widely
+    (a few heavy rows; per-row scales 10^U(-2, 2)).  Both against the oracle; with uniform
+    draws A_s^T A_s misses the rows that matter and PCG needs several times more iterations."""
+    import workloads as W2
+    mat = _heavy_rows() if case == "heavy_rows" else W2.sparse_random(20000, 300, 8, 3)
+    Mx, keep, seen = to_device(lsq, mat)
+    o = lsq.opts(seed=5, sampling=1 if sampling == "uniform" else 0)
+    idx, p, d = lsq.lsq_sample_rows(Mx, o)
+    P = lsq.lsq_build_precond(Mx, idx, p, d, o)
+    smp = orc.Sample(seen, seed=5, sampling=sampling)
+    assert np.array_equal(idx.cpu().numpy(), smp.idx)
+    Mo = orc.SampledM(smp)
+    xs, b = W.rhs_for(seen, 1, 1e-3, 6)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+    A = seen["A"] if seen["kind"] == "dense" else W.dense_from_csr(seen)
+    kappa = np.linalg.cond(A / smp.d)
+    assert info.converged[0] == 1 and oi["converged"] == 1
+    assert_solution(X.cpu().numpy().reshape(-1), y / smp.d, kappa, f"{case} {sampling}")
+    assert_iterations(info.iters[0], oi["iters"],
+                      lambda: rounding_variant_iters(orc, seen, smp, Mo, b[0], o.tol, 1, o.maxit, o.max_outer),
+                      f"{case} {sampling} sampling")
+    if sampling == "uniform":
+        nrm = orc.Sample(seen, seed=5)
+        y2, oi2 = orc.pcg(nrm.mat, nrm.d, orc.SampledM(nrm), b=b[0], tol=o.tol, maxit=o.maxit,
+                          max_outer=o.max_outer)
+        assert info.iters[0] > 2 * oi2["iters"], (info.iters[0], oi2["iters"])
+
+
 def test_pcg_deterministic(lsq, orc):
     mat = W.gaussian_dense(4096, 128, 1001)
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1001)

@@ -526,3 +526,70 @@ def test_iteration_counts_match_paper_tables(orc, row):
     assert abs(counts[0][0] - it_cg) <= 1, (counts, it_cg)
     lo, hi = rs_mean - 3 * rs_std - 1, rs_mean + 3 * rs_std + 1
     assert all(lo <= c <= hi for c in counts[5]), (counts[5], rs_mean, rs_std)
+
+
+# ---------------------------------------------------------------------------------------
+# The uniform density of the comparison in Sec. 3.1 (p_i = 1/m) and why the method does not
+# use it: on a coherent matrix uniform draws miss the rows that carry the columns.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [777, 4096])
+def test_uniform_draws_are_floor_of_U_times_m(orc, m):
+    """With every weight 1 the draw of Alg. 1 is i_t = floor(U_t m / 2^128), U_t the 128-bit
+    word of Philox block t: computed here from numpy's independent Philox and Python ints."""
+    mat = W.gaussian_dense(m, 5, 3)
+    smp = orc.Sample(mat, seed=99, s=300, sampling="uniform")
+    key = np.array([99, 0x5A4D504C], dtype=np.uint64)
+    want = []
+    for t in range(300):
+        ctr = (t - 1) % (1 << 256)
+        words = [(ctr >> (64 * i)) & ((1 << 64) - 1) for i in range(4)]
+        raw = [int(v) for v in np.random.Philox(key=key, counter=np.array(words, dtype=np.uint64)).random_raw(2)]
+        U = (raw[1] << 64) | raw[0]
+        want.append((U * m) >> 128)
+    assert smp.idx.tolist() == want
+
+
+def test_uniform_draws_are_uniform(orc):
+    m, s = 64, 64000
+    smp = orc.Sample(W.gaussian_dense(m, 4, 5), seed=3, s=s, sampling="uniform")
+    counts = np.bincount(smp.idx, minlength=m)
+    chi2 = float(((counts - s / m) ** 2 / (s / m)).sum())
+    assert chi2 < 120.0          # 63 degrees of freedom: the 0.9999 quantile is about 115
+
+
+def test_uniform_sampling_misses_the_rows_of_a_coherent_matrix(orc):
+    """Z = [I; 0] (Sec. 3.1): the norm-squared density draws only the n identity rows, so
+    every column of A_s^T A_s is sampled; uniform draws almost always land on zero rows, so
+    most diagonal entries of A_s^T A_s stay zero (replaced by 1) and A_s^T A_s is a poor
+    approximation of A^T A = I."""
+    m, n = 4000, 40
+    mat = W.coherent_dense(m, n)
+    s = orc.sample_size(n)
+    nrm = orc.Sample(mat, seed=5)
+    uni = orc.Sample(mat, seed=5, sampling="uniform")
+    assert nrm.idx.max() < n and len(set(nrm.idx.tolist())) == n
+    hits = int((uni.idx < n).sum())
+    assert hits < 0.1 * s                     # about s n / m = 24 of 591 draws
+    Mn, Mu = orc.SampledM(nrm), orc.SampledM(uni)
+    assert Mn.n_fixed_diag == 0 and Mu.n_fixed_diag >= n // 2
+    # with the method's density M is diag(counts) n / s, near the identity (Sec. 3.2); the
+    # uniform draws that do hit an identity row weigh m / s each, far from it
+    assert np.abs(Mn.dense() - np.eye(n)).max() < 1.0 < np.abs(Mu.dense() - np.eye(n)).max()
+
+
+def test_uniform_sampling_is_a_weaker_preconditioner_when_rows_differ(orc):
+    """Sec. 3.1 on a matrix whose columns are carried by a few rows (400 Gaussian rows of
+    20000; the rest scaled by 1e-3): PCG with the norm-squared density converges in a
+    fraction of the iterations that uniform sampling needs (measured 18 against 96)."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((20000, 100))
+    A[400:] *= 1e-3
+    mat = {"kind": "dense", "A": A}
+    xs, b = W.rhs_for(mat, 1, 1e-3, 6)
+    its = {}
+    for sampling in ("norm2", "uniform"):
+        smp = orc.Sample(mat, seed=5, sampling=sampling)
+        y, oi = orc.pcg(smp.mat, smp.d, orc.SampledM(smp), b=b[0], tol=1e-10, maxit=10000, max_outer=20)
+        assert oi["converged"] == 1
+        its[sampling] = oi["iters"]
+    assert its["norm2"] <= 25 and its["uniform"] >= 3 * its["norm2"], its

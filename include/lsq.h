@@ -325,6 +325,42 @@ LSQ_API lsq_status lsq_batch_set_cluster(lsq_batch* b, int32_t cluster);
 LSQ_API lsq_status lsq_batch_info(const lsq_batch* b, lsq_info* infos, void* stream);
 LSQ_API void lsq_batch_destroy(lsq_batch* b);
 
+/*
+ * Row-sharded sampling (the multi-GPU design of the sampling steps; not in the paper, which
+ * runs on one machine).  Rank r holds the rows [row0, row0 + A->m) of the whole matrix as
+ * its own lsq_matrix.  Because the sampling law of lsq_sample_rows is exact integer
+ * arithmetic, the cross-rank steps are plain integer collectives done by the caller, and
+ * the merged draws equal one process's lsq_sample_rows bit for bit:
+ *   1. lsq_shard_colmax   colmax[j] = max_i |a_ij| (FP64 bit patterns)  -> all-reduce MAX
+ *   2. lsq_shard_colsum   the exact column sums c_j of Alg. 2 step 1 as four 32-bit limbs,
+ *                         limbs[4j + k] (int64)                           -> all-reduce SUM
+ *   3. lsq_shard_weights  d_j (the same on every rank) and the rank's prefix of the row
+ *                         weights of Eq. (R2P); W_local_limbs (host) = the rank's total
+ *                                                                      -> all-gather
+ *   4. lsq_shard_offsets  the rank's offset and the grand total from the gathered totals
+ *                         (host only)
+ *   5. lsq_shard_draw     every draw t of Alg. 1 against the grand total; idx_out[t] is the
+ *                         global row when the draw falls in this rank's range, else -1,
+ *                         and p_out[t] the row's probability, else 0    -> all-reduce MAX
+ * Arrays named "device" are device memory; colmax has n entries, limbs 4n, prefix
+ * (A->m + 1) x 16 bytes (16-byte aligned), idx_out and p_out s entries.  Status and errors as
+ * lsq_sample_rows.  lsq_shard_draw_host is step 5 for a prefix held in host memory (two
+ * 64-bit words per entry, low first), for draws t0 .. t0 + s - 1.
+ */
+LSQ_API lsq_status lsq_shard_colmax(const lsq_matrix* A, uint64_t* colmax, void* stream);
+LSQ_API lsq_status lsq_shard_colsum(const lsq_matrix* A, const uint64_t* colmax, int64_t* limbs, void* stream);
+LSQ_API lsq_status lsq_shard_weights(const lsq_matrix* A, const lsq_opts* o, const uint64_t* colmax,
+                                     const int64_t* limbs, double* colscale_out, void* prefix,
+                                     int64_t* W_local_limbs, void* stream);
+LSQ_API lsq_status lsq_shard_offsets(const int64_t* W_all, int32_t world, int32_t rank, int64_t* W_offset,
+                                     int64_t* W_total);
+LSQ_API lsq_status lsq_shard_draw(const void* prefix, int64_t m_local, int64_t row0, const int64_t* W_offset,
+                                  const int64_t* W_total, const lsq_opts* o, int64_t s, int32_t* idx_out,
+                                  double* p_out, void* stream);
+LSQ_API lsq_status lsq_shard_draw_host(const uint64_t* prefix, int64_t m_local, int64_t row0,
+                                       const int64_t* W_offset, const int64_t* W_total, uint64_t seed,
+                                       int64_t t0, int64_t s, int32_t* idx_out);
+
 /* Convert FP64 values to the LSQ_F32X2 pair format (hi = RN(v), lo = RN(v - hi)),
  * count elements, device to device (a storage form of this library, not in the paper).
  * LSQ_ERR_INVALID for NULL pointers or count < 0; count = 0 launches nothing. */

@@ -66,6 +66,12 @@ PROTOTYPES = {
     "lsq_last_error_string": (C.c_char_p, []),
     "lsq_kernel_launch_count": (I64, []),
     "lsq_set_wait_limit": (C.c_int, [I64]),
+    "lsq_shard_colmax": (C.c_int, [P, P, P]),
+    "lsq_shard_colsum": (C.c_int, [P, P, P, P]),
+    "lsq_shard_weights": (C.c_int, [P, P, P, P, P, P, P, P]),
+    "lsq_shard_offsets": (C.c_int, [P, C.c_int32, C.c_int32, P, P]),
+    "lsq_shard_draw": (C.c_int, [P, I64, I64, P, P, P, I64, P, P, P]),
+    "lsq_shard_draw_host": (C.c_int, [P, I64, I64, P, P, C.c_uint64, I64, I64, P]),
 }
 
 _lock = threading.Lock()

@@ -266,6 +266,69 @@ def launches() -> int:
     return int(L.load().lsq_kernel_launch_count())
 
 
+# Row-sharded sampling (lsq_shard_* in lsq.h): one rank's phases; the caller does the
+# collectives between them (MAX of colmax, SUM of limbs, all-gather of the totals, MAX merge
+# of the draws).  colmax travels as int64 (bit patterns of non-negative doubles, below 2^63).
+def shard_colmax(A: Matrix, stream=None):
+    out = torch.empty(A.n, dtype=torch.int64, device=A.vals.device)
+    _check(L.load().lsq_shard_colmax(A.ref, _ptr(out), _stream(stream)), "lsq_shard_colmax")
+    return out
+
+
+def shard_colsum(A: Matrix, colmax, stream=None):
+    _device_array(colmax, "colmax", torch.int64)
+    limbs = torch.empty(4 * A.n, dtype=torch.int64, device=A.vals.device)
+    _check(L.load().lsq_shard_colsum(A.ref, _ptr(colmax), _ptr(limbs), _stream(stream)), "lsq_shard_colsum")
+    return limbs
+
+
+def shard_weights(A: Matrix, colmax, limbs, o=None, stream=None):
+    """-> (colscale d, the rank's weight prefix as int64 (m + 1, 2), its total as 4 limbs)."""
+    o = o or opts()
+    _device_array(colmax, "colmax", torch.int64)
+    _device_array(limbs, "limbs", torch.int64)
+    d = torch.empty(A.n, dtype=torch.float64, device=A.vals.device)
+    prefix = torch.empty(A.m + 1, 2, dtype=torch.int64, device=A.vals.device)
+    W = np.zeros(4, np.int64)
+    _check(L.load().lsq_shard_weights(A.ref, C.byref(o), _ptr(colmax), _ptr(limbs), _ptr(d), _ptr(prefix),
+                                      W.ctypes.data, _stream(stream)), "lsq_shard_weights")
+    return d, prefix, W
+
+
+def shard_offsets(W_all, rank: int):
+    """W_all: (world, 4) int64 limbs of every rank's total -> (offset, total) limbs."""
+    W_all = np.ascontiguousarray(W_all, np.int64)
+    off, tot = np.zeros(4, np.int64), np.zeros(4, np.int64)
+    _check(L.load().lsq_shard_offsets(W_all.ctypes.data, W_all.shape[0], int(rank), off.ctypes.data,
+                                      tot.ctypes.data), "lsq_shard_offsets")
+    return off, tot
+
+
+def shard_draw(prefix, row0: int, W_offset, W_total, s: int, o=None, stream=None):
+    """-> (idx int32[s]: global row or -1, p float64[s]: its probability or 0)."""
+    o = o or opts()
+    _device_array(prefix, "prefix", torch.int64)
+    off = np.ascontiguousarray(W_offset, np.int64)
+    tot = np.ascontiguousarray(W_total, np.int64)
+    idx = torch.empty(s, dtype=torch.int32, device=prefix.device)
+    p = torch.empty(s, dtype=torch.float64, device=prefix.device)
+    _check(L.load().lsq_shard_draw(_ptr(prefix), prefix.shape[0] - 1, int(row0), off.ctypes.data, tot.ctypes.data,
+                                   C.byref(o), int(s), _ptr(idx), _ptr(p), _stream(stream)), "lsq_shard_draw")
+    return idx, p
+
+
+def shard_draw_host(prefix, row0: int, W_offset, W_total, seed: int, t0: int, s: int):
+    """lsq_shard_draw on a host prefix (uint64 array of (m + 1) x 2 words) -> int32[s]."""
+    prefix = np.ascontiguousarray(prefix, np.uint64)
+    off = np.ascontiguousarray(W_offset, np.int64)
+    tot = np.ascontiguousarray(W_total, np.int64)
+    idx = np.empty(s, np.int32)
+    _check(L.load().lsq_shard_draw_host(prefix.ctypes.data, prefix.size // 2 - 1, int(row0), off.ctypes.data,
+                                        tot.ctypes.data, C.c_uint64(seed), int(t0), int(s), idx.ctypes.data),
+           "lsq_shard_draw_host")
+    return idx
+
+
 def set_wait_limit(max_polls: int = 0):
     """Cap every device-side wait at max_polls polls (0: the library's defaults)."""
     _check(L.load().lsq_set_wait_limit(int(max_polls)), "lsq_set_wait_limit")

@@ -352,6 +352,60 @@ __global__ void k_draw(const u128* P, int64_t m, int64_t s, unsigned long long s
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Row-sharded sampling: a rank holds a contiguous block of rows.  The exact integer law
+// makes the cross-rank steps plain integer collectives: column maxima (MAX), exact column
+// sums (SUM of 32-bit limbs), the ranks' weight totals (all-gather), and the merge of the
+// draws (MAX over -1 / row index), so the indices equal one process's bit for bit.
+// ---------------------------------------------------------------------------------------
+__global__ void k_u128_to_limbs(int64_t n, const u128* c, int64_t* limbs) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const u128 v = c[j];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) limbs[4 * j + k] = (int64_t)(unsigned long long)((v >> (32 * k)) & 0xFFFFFFFFull);
+    }
+}
+// limbs (each a sum of 32-bit limbs over the ranks, < 2^63) back to u128 with the carries
+__global__ void k_limbs_to_u128(int64_t n, const int64_t* limbs, u128* c) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        u128 v = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v += (u128)(unsigned long long)limbs[4 * j + k] << (32 * k);
+        c[j] = v;
+    }
+}
+// Draws t = 0..s-1 of Alg. 1 against the whole matrix's total W; a rank keeps those whose
+// target falls in its range [O, O + W_r) and finds the row in its local prefix.
+__global__ void k_draw_shard(const u128* P, int64_t m, int64_t row0, unsigned long long O_lo,
+                             unsigned long long O_hi, unsigned long long W_lo, unsigned long long W_hi,
+                             int64_t s, unsigned long long seed, int32_t* idx, double* p_out) {
+    const u128 O = ((u128)O_hi << 64) | O_lo, W = ((u128)W_hi << 64) | W_lo;
+    const u128 Wr = P[m];
+    const double Wd = u128_to_double_rn(W);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < s;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long c[4] = {(unsigned long long)t, 0ull, 0ull, 0ull};
+        philox4x64_10(c, seed, 0x5A4D504Cull);
+        const u128 U = ((u128)c[1] << 64) | c[0];
+        const u128 target = mulhi_u128(U, W);
+        if (target < O || target - O >= Wr) {
+            idx[t] = -1;
+            if (p_out) p_out[t] = 0.0;
+            continue;
+        }
+        const u128 local = target - O;
+        int64_t lo = 0, hi = m;  // P[lo] <= local < P[hi]
+        while (hi - lo > 1) {
+            int64_t mid = lo + ((hi - lo) >> 1);
+            if (P[mid] <= local) lo = mid; else hi = mid;
+        }
+        idx[t] = (int32_t)(row0 + lo);
+        if (p_out) p_out[t] = __ddiv_rn(u128_to_double_rn(P[lo + 1] - P[lo]), Wd);
+    }
+}
+
 static int grid_for(int64_t work, int threads, int cap = 152 * 16) {
     int64_t g = (work + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -557,4 +611,242 @@ extern "C" lsq_status lsq_sample_rows_static(const lsq_matrix* A, const lsq_opts
     }
     set_error("unknown dtype");
     return LSQ_ERR_INVALID;
+}
+
+// ---------------------------------------------------------------------------------------
+// Row-sharded sampling entry points (declared in lsq.h)
+// ---------------------------------------------------------------------------------------
+namespace {
+template <int DT>
+lsq_status shard_colmax_impl(const lsq_matrix* A, unsigned long long* amax, unsigned* err, cudaStream_t st) {
+    lsq_matrix Av = *A;
+    if (A->dense) {
+        int64_t rpb = (A->m + 152 * 8 - 1) / (152 * 8);
+        if (rpb < 16) rpb = 16;
+        k_colmax_dense<DT><<<(int)((A->m + rpb - 1) / rpb), 256, 0, st>>>(Av, amax, err, rpb);
+    } else {
+        k_colmax_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, amax, err);
+    }
+    count_launch();
+    return LSQ_OK;
+}
+template <int DT>
+lsq_status shard_colsum_impl(const lsq_matrix* A, const int* E1j, u128* c, cudaStream_t st) {
+    lsq_matrix Av = *A;
+    if (A->dense) {
+        int64_t rpb = (A->m + 152 * 8 - 1) / (152 * 8);
+        if (rpb < 16) rpb = 16;
+        k_colsum_dense<DT><<<(int)((A->m + rpb - 1) / rpb), 256, 0, st>>>(Av, E1j, c, rpb);
+    } else {
+        k_colsum_csr<DT><<<grid_for(A->nnz, 256), 256, 0, st>>>(Av, E1j, c);
+    }
+    count_launch();
+    return LSQ_OK;
+}
+template <template <int> class F, typename... Args>
+lsq_status by_dtype(int dtype, Args... args) {
+    switch (dtype) {
+        case LSQ_F64: return F<LSQ_F64>::run(args...);
+        case LSQ_F32: return F<LSQ_F32>::run(args...);
+        case LSQ_BF16: return F<LSQ_BF16>::run(args...);
+        case LSQ_F32X2: return F<LSQ_F32X2>::run(args...);
+    }
+    set_error("unknown dtype");
+    return LSQ_ERR_INVALID;
+}
+template <int DT> struct ColmaxF {
+    static lsq_status run(const lsq_matrix* A, unsigned long long* amax, unsigned* err, cudaStream_t st) {
+        return shard_colmax_impl<DT>(A, amax, err, st);
+    }
+};
+template <int DT> struct ColsumF {
+    static lsq_status run(const lsq_matrix* A, const int* E1j, u128* c, cudaStream_t st) {
+        return shard_colsum_impl<DT>(A, E1j, c, st);
+    }
+};
+template <int DT> struct WeightF {
+    static lsq_status run(const lsq_matrix* A, const double* inv, u128* w, int uniform, cudaStream_t st) {
+        k_rowweight<DT><<<grid_for(A->m * 32, 256), 256, 0, st>>>(*A, inv, w, uniform);
+        count_launch();
+        return LSQ_OK;
+    }
+};
+void to_limbs(u128 v, int64_t* out) {
+    for (int k = 0; k < 4; ++k) out[k] = (int64_t)(unsigned long long)((v >> (32 * k)) & 0xFFFFFFFFull);
+}
+u128 from_limbs(const int64_t* l) {
+    u128 v = 0;
+    for (int k = 0; k < 4; ++k) v += (u128)(unsigned long long)l[k] << (32 * k);
+    return v;
+}
+}  // namespace
+
+extern "C" lsq_status lsq_shard_colmax(const lsq_matrix* A, uint64_t* colmax, void* stream) {
+    lsq_status st0 = check_matrix(A);
+    if (st0 != LSQ_OK) return st0;
+    LSQ_CHECK_ARG(colmax != nullptr, "colmax is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc;
+    LSQ_CUDA(sc.alloc(16, st));
+    unsigned* err = sc.as<unsigned>();
+    LSQ_CUDA(cudaMemsetAsync(err, 0, 16, st));
+    LSQ_CUDA(cudaMemsetAsync(colmax, 0, 8 * (size_t)A->n, st));
+    lsq_status r = by_dtype<ColmaxF>(A->dtype, A, (unsigned long long*)colmax, err, st);
+    if (r != LSQ_OK) return r;
+    LSQ_CUDA(cudaGetLastError());
+    return read_dev_error(err, st);
+}
+
+extern "C" lsq_status lsq_shard_colsum(const lsq_matrix* A, const uint64_t* colmax, int64_t* limbs, void* stream) {
+    lsq_status st0 = check_matrix(A);
+    if (st0 != LSQ_OK) return st0;
+    LSQ_CHECK_ARG(colmax != nullptr && limbs != nullptr, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = A->n;
+    Scratch sc;
+    LSQ_CUDA(sc.alloc(256 + 4 * (size_t)n + 16 * (size_t)n + 256, st));
+    char* base = sc.as<char>();
+    unsigned* err = (unsigned*)base;
+    unsigned* E1g = err + 4;
+    int* E1j = (int*)(base + 256);
+    u128* c = (u128*)(base + 256 + ((4 * (size_t)n + 255) & ~(size_t)255));
+    LSQ_CUDA(cudaMemsetAsync(err, 0, 16, st));
+    LSQ_CUDA(cudaMemsetAsync(E1g, 0xff, 4, st));
+    LSQ_CUDA(cudaMemsetAsync(c, 0, 16 * (size_t)n, st));
+    k_col_exponents<<<grid_for(n, 256), 256, 0, st>>>(n, (const unsigned long long*)colmax, E1j, E1g, err);
+    count_launch();
+    lsq_status r = by_dtype<ColsumF>(A->dtype, A, (const int*)E1j, c, st);
+    if (r != LSQ_OK) return r;
+    k_u128_to_limbs<<<grid_for(n, 256), 256, 0, st>>>(n, c, limbs);
+    count_launch();
+    LSQ_CUDA(cudaGetLastError());
+    return read_dev_error(err, st);
+}
+
+extern "C" lsq_status lsq_shard_weights(const lsq_matrix* A, const lsq_opts* o, const uint64_t* colmax,
+                                        const int64_t* limbs, double* colscale_out, void* prefix,
+                                        int64_t* W_local_limbs, void* stream) {
+    lsq_status st0 = check_matrix(A);
+    if (st0 != LSQ_OK) return st0;
+    LSQ_CHECK_ARG(o && colmax && limbs && colscale_out && prefix && W_local_limbs, "NULL argument");
+    LSQ_CHECK_ARG(o->sampling == 0 || o->sampling == 1, "sampling must be 0 (norm squared) or 1 (uniform)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t m = A->m, n = A->n;
+    const int64_t ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t at = off; off += (b + 255) & ~size_t(255); return at; };
+    const size_t o_err = take(16), o_E1g = take(16), o_E1j = take(4 * n), o_c = take(16 * n),
+                 o_d2 = take(8 * n), o_inv = take(8 * n), o_w = take(16 * m), o_ts = take(16 * ntiles);
+    Scratch sc;
+    LSQ_CUDA(sc.alloc(off, st));
+    char* base = sc.as<char>();
+    unsigned* err = (unsigned*)(base + o_err);
+    unsigned* E1g = (unsigned*)(base + o_E1g);
+    int* E1j = (int*)(base + o_E1j);
+    u128* c = (u128*)(base + o_c);
+    double* d2 = (double*)(base + o_d2);
+    double* inv = (double*)(base + o_inv);
+    u128* w = (u128*)(base + o_w);
+    u128* ts = (u128*)(base + o_ts);
+    u128* P = (u128*)prefix;
+    LSQ_CUDA(cudaMemsetAsync(err, 0, 16, st));
+    LSQ_CUDA(cudaMemsetAsync(E1g, 0xff, 4, st));
+    k_col_exponents<<<grid_for(n, 256), 256, 0, st>>>(n, (const unsigned long long*)colmax, E1j, E1g, err);
+    k_limbs_to_u128<<<grid_for(n, 256), 256, 0, st>>>(n, limbs, c);
+    k_colscale<<<grid_for(n, 256), 256, 0, st>>>(n, o->normalize ? 1 : 0, E1j, E1g, c, d2, inv, colscale_out);
+    count_launch(3);
+    lsq_status r = by_dtype<WeightF>(A->dtype, A, (const double*)inv, w, o->sampling == 1 ? 1 : 0, st);
+    if (r != LSQ_OK) return r;
+    k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts);
+    k_scan_sums<<<1, 1024, 0, st>>>(ts, ntiles);
+    k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(w, m, ts, P);
+    count_launch(3);
+    u128 Wr = 0;
+    LSQ_CUDA(cudaMemcpyAsync(&Wr, P + m, sizeof(u128), cudaMemcpyDeviceToHost, st));
+    lsq_status e = read_dev_error(err, st);   // synchronises the stream
+    if (e != LSQ_OK) return e;
+    to_limbs(Wr, W_local_limbs);
+    return LSQ_OK;
+}
+
+extern "C" lsq_status lsq_shard_offsets(const int64_t* W_all, int32_t world, int32_t rank, int64_t* W_offset,
+                                        int64_t* W_total) {
+    LSQ_CHECK_ARG(W_all && W_offset && W_total, "NULL argument");
+    LSQ_CHECK_ARG(world >= 1 && rank >= 0 && rank < world, "rank must lie in [0, world)");
+    u128 O = 0, W = 0;
+    for (int r = 0; r < world; ++r) {
+        const u128 v = from_limbs(W_all + 4 * (int64_t)r);
+        if (r < rank) O += v;
+        W += v;
+    }
+    to_limbs(O, W_offset);
+    to_limbs(W, W_total);
+    return LSQ_OK;
+}
+
+extern "C" lsq_status lsq_shard_draw(const void* prefix, int64_t m_local, int64_t row0, const int64_t* W_offset,
+                                     const int64_t* W_total, const lsq_opts* o, int64_t s, int32_t* idx_out,
+                                     double* p_out, void* stream) {
+    LSQ_CHECK_ARG(prefix && W_offset && W_total && o && idx_out, "NULL argument");
+    LSQ_CHECK_ARG(m_local >= 1 && row0 >= 0 && row0 + m_local <= ((int64_t)1 << 31), "bad row range");
+    LSQ_CHECK_ARG(s > 0 && s < (int64_t)1 << 40, "sample size out of range");
+    const u128 O = from_limbs(W_offset), W = from_limbs(W_total);
+    if (W == 0) { set_error("no row has positive sampling weight"); return LSQ_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    k_draw_shard<<<grid_for(s, 256), 256, 0, st>>>((const u128*)prefix, m_local, row0, (unsigned long long)O,
+                                                   (unsigned long long)(O >> 64), (unsigned long long)W,
+                                                   (unsigned long long)(W >> 64), s, (unsigned long long)o->seed,
+                                                   idx_out, p_out);
+    count_launch();
+    LSQ_CUDA(cudaGetLastError());
+    return LSQ_OK;
+}
+
+// The same filtered draws on the host, for a prefix held in host memory (two 64-bit words
+// per entry, low word first): Philox4x64-10 (Salmon et al., SC'11), the high 128 bits of
+// U W, and the search in the local prefix, as in k_draw_shard.
+namespace {
+void philox_host(unsigned long long c[4], unsigned long long k0, unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    for (int r = 0; r < 10; ++r) {
+        const u128 p0 = (u128)M0 * c[0], p1 = (u128)M1 * c[2];
+        const unsigned long long n0 = (unsigned long long)(p1 >> 64) ^ c[1] ^ k0;
+        const unsigned long long n2 = (unsigned long long)(p0 >> 64) ^ c[3] ^ k1;
+        c[0] = n0; c[1] = (unsigned long long)p1; c[2] = n2; c[3] = (unsigned long long)p0;
+        k0 += W0; k1 += W1;
+    }
+}
+u128 mulhi_host(u128 a, u128 b) {
+    const unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
+    const unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
+    const u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+    const u128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
+    return p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+}
+}  // namespace
+
+extern "C" lsq_status lsq_shard_draw_host(const uint64_t* prefix, int64_t m_local, int64_t row0,
+                                          const int64_t* W_offset, const int64_t* W_total, uint64_t seed,
+                                          int64_t t0, int64_t s, int32_t* idx_out) {
+    LSQ_CHECK_ARG(prefix && W_offset && W_total && idx_out, "NULL argument");
+    LSQ_CHECK_ARG(m_local >= 1 && row0 >= 0 && t0 >= 0 && s >= 0, "bad range");
+    const u128 O = from_limbs(W_offset), W = from_limbs(W_total);
+    LSQ_CHECK_ARG(W != 0, "no row has positive sampling weight");
+    auto P = [&](int64_t i) { return ((u128)prefix[2 * i + 1] << 64) | prefix[2 * i]; };
+    const u128 Wr = P(m_local);
+    for (int64_t k = 0; k < s; ++k) {
+        unsigned long long c[4] = {(unsigned long long)(t0 + k), 0ull, 0ull, 0ull};
+        philox_host(c, seed, 0x5A4D504Cull);
+        const u128 target = mulhi_host(((u128)c[1] << 64) | c[0], W);
+        if (target < O || target - O >= Wr) { idx_out[k] = -1; continue; }
+        const u128 local = target - O;
+        int64_t lo = 0, hi = m_local;
+        while (hi - lo > 1) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (P(mid) <= local) lo = mid; else hi = mid;
+        }
+        idx_out[k] = (int32_t)(row0 + lo);
+    }
+    return LSQ_OK;
 }

@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch", "tc", "sampling"],
                     default="udv",
                     help="udv: the timed benchmark; the others measure one other configuration alone")
+    ap.add_argument("--device-loop", type=int, default=0,
+                    help="CSR blocks of right-hand sides: 1 = one persistent launch per solve")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations and the FP64 comparison solve after the timed region")
     return ap.parse_args()
@@ -541,7 +543,7 @@ def oracle_csr_sample(mat, b, seed, iters_gpu, k, cpu_iters=3):
 
 
 def sparse_config(which, tol=1e-10, maxit=1000000, sweeps=1, inner_tol=0.0, steps=3, warmup=1,
-                  cpu=True, mat=None):
+                  cpu=True, mat=None, device_loop=0):
     """One CSR configuration: sparse random 4e6 x 4e4 (FP32 values, FP64 refinement), weighted
     graph incidence with 32 right-hand sides (FP64), or sparse 1e6 x 1e4 with 16 right-hand
     sides through the solve and the adjoint (FP32 values, FP64 refinement).  A step is
@@ -559,7 +561,7 @@ def sparse_config(which, tol=1e-10, maxit=1000000, sweeps=1, inner_tol=0.0, step
     vals = v64.float() if dt == "f32" else v64
     Mx = api.Matrix(row_ptr=rp, col_idx=ci, vals=vals, n=mat["n"], vals_f64=v64 if dt == "f32" else None)
     o = api.opts(seed=1003, tol=tol, maxit=maxit, max_outer=50, inner_tol=inner_tol, sweeps=sweeps,
-                 precond_dtype=1 if dt == "f32" else 0)
+                 precond_dtype=1 if dt == "f32" else 0, device_loop=device_loop)
     B = torch.from_numpy(b).cuda()
     runs = []
     L0 = api.launches()
@@ -593,7 +595,8 @@ def sparse_config(which, tol=1e-10, maxit=1000000, sweeps=1, inner_tol=0.0, step
     out = {"value": k / tot, "unit": "solves/s (right-hand sides)", "ms_per_step": tot * 1e3,
            "steps": steps, "warmup": warmup, "dtype": dt + ("+f64" if dt == "f32" else ""),
            "config": {"workload": name, "m": int(mat["m"]), "n": int(mat["n"]), "k": k, "tol": tol,
-                      "sweeps": sweeps, "nnz_A": int(mat["row_ptr"][-1]), "nnz_M": int(info.nnz_M),
+                      "sweeps": sweeps, "device_loop": device_loop,
+                      "nnz_A": int(mat["row_ptr"][-1]), "nnz_M": int(info.nnz_M),
                       "levels": int(info.levels), "s": int(info.s)},
            "iters_max": it, "iters": info.iters.tolist() if k <= 4 else None,
            "converged": int(np.sum(info.converged)), "relres_true_max": float(np.max(info.relres_true)),
@@ -616,7 +619,7 @@ def run_sparse_workload(args):
     pkg.build()
     torch.cuda.set_device(0)
     out = sparse_config(args.workload, args.tol, args.maxit, args.sweeps, args.inner_tol,
-                        args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+                        args.steps, args.warmup, cpu=not args.no_cpu_baseline, device_loop=args.device_loop)
     line = {"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
 

@@ -98,6 +98,11 @@ typedef struct {
     int32_t sampling;      /* row sampling density of Alg. 1: 0 = p_i proportional to the squared
                               row norm (Eq. R2P, the method); 1 = uniform p_i = 1/m (the
                               comparison of Sec. 3.1, which coherent matrices defeat); 0 */
+    int32_t device_loop;   /* CSR A, k >= 2 columns, FP64 or FP32 values: 1 = the whole solve in
+                              one persistent launch, no host decision or synchronisation until
+                              the results are read; 0 = stream-ordered kernels with the loop on
+                              the host (their passes keep more warps resident).  Under stream
+                              capture the persistent form is always used; 0 */
 } lsq_opts;
 
 /* Per-right-hand-side results, written to caller-owned HOST arrays of length k (any
@@ -238,10 +243,14 @@ LSQ_API lsq_status lsq_precond_apply(const lsq_precond* P, const double* r, doub
  *
  * Dense A (values F64, F32, BF16 or F32X2): the whole loop of each column runs inside one
  * persistent cooperative kernel.  FP32 and BF16 values are products and sums in FP32 (BF16
- * widened exactly on load), F32X2 in double-float, with FP64 restarts from vals_f64.  CSR A (values F64, F32,
- * BF16 or F32X2; P built with sweeps <= 32): each iteration is a row pass, a column pass
- * and the level-ordered sweeps of Alg. 3; k >= 2 columns advance together in blocks of up
- * to 32, with one pass over A and one sweep per iteration for the whole block.
+ * widened exactly on load), F32X2 in double-float, with FP64 restarts from vals_f64.
+ * CSR A (values F64, F32, BF16 or F32X2; P built with sweeps <= 32): each iteration is a
+ * row pass, a column pass and the level-ordered sweeps of Alg. 3; k >= 2 columns advance
+ * together in blocks of up to 32, with one pass over A and one sweep per iteration for the
+ * whole block.  With o->device_loop = 1, or when the stream is being captured, a block with
+ * FP64 or FP32 values runs as ONE persistent cooperative launch.  Under stream capture the
+ * call writes X from the graph, reports no per-column results (info is left untouched) and
+ * returns LSQ_OK; other value types return LSQ_ERR_UNSUPPORTED there.
  *
  *   A      matrix (device)
  *   P      handle built for this A

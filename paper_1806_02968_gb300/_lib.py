@@ -23,7 +23,7 @@ class LsqOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("max_outer", C.c_int32),
                 ("sweeps", C.c_int32), ("sample_factor", C.c_double), ("normalize", C.c_int32),
                 ("precond_dtype", C.c_int32), ("seed", C.c_uint64), ("inner_tol", C.c_double),
-                ("grid_ctas", C.c_int32), ("sampling", C.c_int32)]
+                ("grid_ctas", C.c_int32), ("sampling", C.c_int32), ("device_loop", C.c_int32)]
 
 
 class LsqInfo(C.Structure):

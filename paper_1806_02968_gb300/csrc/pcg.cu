@@ -256,6 +256,7 @@ extern "C" lsq_status lsq_pcg_solve(const lsq_matrix* A, const lsq_precond* P, c
     LSQ_CHECK_ARG(k >= 1, "k must be >= 1");
     LSQ_CHECK_ARG(ldb >= A->m && ldx >= A->n, "ldb >= m and ldx >= n required");
     LSQ_CHECK_ARG(o->tol > 0 && o->maxit >= 0 && o->max_outer >= 1, "bad tolerance or caps");
+    LSQ_CHECK_ARG(o->device_loop == 0 || o->device_loop == 1, "device_loop must be 0 or 1");
     if (!A->dense) {
         lsq_status s0 = check_matrix(A);
         if (s0 != LSQ_OK) return s0;

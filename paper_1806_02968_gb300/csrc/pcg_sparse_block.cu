@@ -309,7 +309,7 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     LSQ_CUDA(cudaMemsetAsync(S, 0, sizeof(BkState), st));
     LSQ_CUDA(cudaMemsetAsync(a.rflag_f, 0, 4 * (size_t)2 * n, st));
     LSQ_CUDA(cudaMemsetAsync(a.y, 0, 8 * (size_t)nK, st));
-    if (DT == LSQ_F64 || DT == LSQ_F32) {
+    if ((DT == LSQ_F64 || DT == LSQ_F32) && (capturing || o->device_loop == 1)) {
         // the whole solve in one persistent kernel: no host decision, no synchronisation
         // until the results are read (none at all under stream capture)
         unsigned long long* pbar = (unsigned long long*)(base + o_pbar);

@@ -546,6 +546,7 @@ extern "C" void lsq_default_opts(lsq_opts* o) {
     o->inner_tol = 0.0;
     o->grid_ctas = 0;
     o->sampling = 0;
+    o->device_loop = 0;
 }
 
 extern "C" lsq_status lsq_set_wait_limit(int64_t max_polls) {

@@ -39,7 +39,7 @@ def test_ctypes_struct_layout_matches_c(lsq, tmp_path):
     c = tmp_path / "layout.c"
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lsq.h"\n'
                  'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lsq_matrix), '
-                 'offsetof(lsq_matrix, vals_f64), sizeof(lsq_opts), offsetof(lsq_opts, sampling), '
+                 'offsetof(lsq_matrix, vals_f64), sizeof(lsq_opts), offsetof(lsq_opts, device_loop), '
                  'sizeof(lsq_info), offsetof(lsq_info, solve_ms), offsetof(lsq_opts, seed));'
                  'printf("%zu %zu %zu\\n", sizeof(lsq_batch_problem), offsetof(lsq_batch_problem, P), '
                  'offsetof(lsq_batch_problem, ldx));return 0;}\n')
@@ -48,7 +48,7 @@ def test_ctypes_struct_layout_matches_c(lsq, tmp_path):
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     L = lsq.L
     want = [ctypes.sizeof(L.LsqMatrix), L.LsqMatrix.vals_f64.offset, ctypes.sizeof(L.LsqOpts),
-            L.LsqOpts.sampling.offset, ctypes.sizeof(L.LsqInfo), L.LsqInfo.solve_ms.offset,
+            L.LsqOpts.device_loop.offset, ctypes.sizeof(L.LsqInfo), L.LsqInfo.solve_ms.offset,
             L.LsqOpts.seed.offset, ctypes.sizeof(L.LsqBatchProblem), L.LsqBatchProblem.P.offset,
             L.LsqBatchProblem.ldx.offset]
     assert got == want

@@ -54,9 +54,12 @@ def test_sparse_sweep_wait_timeout_then_recovers(lsq, orc):
     assert abs(int(info.iters[0]) - oi["iters"]) <= 2
 
 
-def test_sparse_block_sweep_wait_timeout(lsq, orc):
-    """The same for a block of right-hand sides (the block sweep forms)."""
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_sparse_block_sweep_wait_timeout(lsq, orc, device_loop):
+    """The same for a block of right-hand sides (the block sweep forms; stream-ordered and the
+    persistent launch, whose grid barriers are capped too)."""
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, W.graph_incidence(20000, 90000, 4), 1003)
+    o.device_loop = device_loop
     xs, b = W.rhs_for(seen, 4, 1e-4, 17)
     B = torch.from_numpy(b).cuda()
     lsq.set_wait_limit(2)
@@ -109,11 +112,12 @@ def test_dense_grid_barrier_timeout_then_recovers(lsq, orc):
     assert_solution(X.cpu().numpy(), y / smp.d, np.linalg.cond(mat["A"] / smp.d), "after timeout")
 
 
-@pytest.mark.parametrize("kind", ["dense", "csr1", "csr3"])
+@pytest.mark.parametrize("kind", ["dense", "csr1", "csr3", "csr3_persistent"])
 def test_breakdown_on_nan_rhs_then_recovers(lsq, orc, kind):
     mat = W.gaussian_dense(4096, 128, 1001) if kind == "dense" else W.sparse_random(20000, 300, 8, 3)
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 1001)
-    k = 3 if kind == "csr3" else 1
+    o.device_loop = 1 if kind == "csr3_persistent" else 0
+    k = 3 if kind.startswith("csr3") else 1
     xs, b = W.rhs_for(seen, k, 1e-3, 5)
     bad = b.copy()
     bad[0, 17] = np.nan

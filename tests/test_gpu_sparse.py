@@ -104,10 +104,12 @@ def test_sparse_f32_values_with_f64_refinement(lsq, orc):
     assert info.converged[0] == 1 and info.relres_true[0] <= o.tol
 
 
-def test_sparse_adjoint_matches_oracle(lsq, orc):
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_sparse_adjoint_matches_oracle(lsq, orc, device_loop):
     mat = W.sparse_random(5000, 60, 6, 2)
     Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 6)
     o.tol = 1e-12
+    o.device_loop = device_loop
     xs, b = W.rhs_for(seen, 2, 1e-2, 8)
     B = torch.from_numpy(b).cuda()
     X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
@@ -283,3 +285,28 @@ def test_sparse_block_solve_captured_in_a_cuda_graph(lsq, orc):
     # one column against the oracle, for good measure
     y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[5], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
     assert_solution(X[5].cpu().numpy(), y / smp.d, np.linalg.cond(W.dense_from_csr(seen) / smp.d), "captured")
+
+
+@pytest.mark.parametrize("case,k,sweeps", [("sprand", 3, 1), ("graph", 4, 2), ("mid", 4, 2), ("sprand", 3, 0),
+                                           ("wide", 2, 1), ("graph_wide", 32, 1)])
+def test_sparse_block_persistent_matches_oracle(lsq, orc, case, k, sweeps):
+    """The persistent form of the block solve (o.device_loop = 1: one cooperative launch for
+    the whole solve, restarts included) against the oracle, for every sweep form (lane per
+    column, lane per entry, CTA per row), t = 0, 1, 2, and blocks of 2 to 32 columns."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 515, sweeps=sweeps)
+    o.device_loop = 1
+    xs, b = W.rhs_for(seen, k, 1e-3, 516)
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
+    small = seen["n"] <= 5000
+    if small:
+        kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
+    for c in range(min(k, 4)):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=sweeps)
+        assert info.converged[c] == 1 and oi["converged"] == 1 and info.relres_true[c] <= o.tol
+        if small:
+            assert_solution(X[c], y / smp.d, kappa, f"persistent {case} column {c}")
+        assert _same_solution(seen, smp.d, X[c], y, b[c], o.tol)
+        assert_iterations(info.iters[c], oi["iters"], _variants(orc, seen, smp, Mo, b[c], o),
+                          f"persistent {case} t={sweeps} column {c}")
+    assert all(info.converged[:k] == 1)

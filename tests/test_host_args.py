@@ -31,7 +31,7 @@ def _err(lsq):
 def test_default_opts_are_the_documented_ones(lsq):
     o = _opts(lsq.L)
     assert (o.tol, o.maxit, o.max_outer, o.sweeps, o.sample_factor, o.normalize, o.precond_dtype,
-            o.seed, o.inner_tol, o.grid_ctas, o.sampling) == (1e-10, 1000000, 20, 1, 4.0, 1, 0, 0, 0.0, 0, 0)
+            o.seed, o.inner_tol, o.grid_ctas, o.sampling, o.device_loop) == (1e-10, 1000000, 20, 1, 4.0, 1, 0, 0, 0.0, 0, 0, 0)
     hdr = open(lsq.L.HERE + "/../include/lsq.h").read()
     for field, text in [("tol", "1e-10"), ("maxit", "1000000"), ("max_outer", "20"),
                         ("sample_factor", "4.0"), ("seed", "0")]:

@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=10)
-    ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch", "tc", "sampling"],
+    ap.add_argument("--workload", choices=["udv", "gauss", "sparse", "graph", "adjoint", "batch", "tc", "sampling",
+                                           "paper"],
                     default="udv",
                     help="udv: the timed benchmark; the others measure one other configuration alone")
     ap.add_argument("--device-loop", type=int, default=0,
@@ -896,6 +897,89 @@ def run_sampling(args):
                       "comparison": sampling_cmp(args.steps, args.warmup)}), flush=True)
 
 
+# The paper's own tables (Sec. 5.1, 5.2, 5.4, 5.5): its sizes, t = 5 sweeps, tolerance 1e-7,
+# s = ceil(4 n ln n), b ~ N(0, 1).  Printed values: iterations of CG on the normalised A and
+# of PCG with the row-sampling preconditioner (RS; a mean over ten runs where the paper gives one).
+PAPER_TABLES = {
+    "gaussian": [((3000, 109), 10, 11), ((5000, 141), 9, 11), ((10000, 200), 9, 11),
+                 ((20000, 282), 8, 11), ((40000, 400), 7, 10.9)],
+    "semi_gaussian": [((1000, 62), 9, 11.7), ((3000, 108), 8, 11.7), ((5000, 140), 8, 11.9),
+                      ((10000, 200), 7, 11.7), ((20000, 282), 7, 11.3)],
+    # kappa(A^T A) as printed; D linear from 1 to sqrt(kappa)
+    "udv_linear_90000x300": [(5936, 116, 23.1), (18853, 202, 38.8), (1.44e5, 294, 72),
+                             (4.75e5, 369, 86.4), (1.07e6, 253, 90.2)],
+    # vertices per glued graph (2 n - 5 vertices: 187 ... 856 in the paper's table)
+    "graph_laplacian_chung_lu": [(96, 40, 16.7), (180, 67, 21.9), (270, 60, 21), (357, 93, 26.8), (430, 112, 30.2)],
+}
+
+
+def paper_tables(steps=1, warmup=1, seeds=5):
+    """Every family of the paper's iteration tables on the GPU, at the printed sizes and
+    settings: CG iterations, RS iterations for `seeds` sampling seeds, and the time of a whole
+    solve (sampling, preconditioner, PCG) for each, beside the printed iteration counts."""
+    import torch
+    import workloads as W
+    from paper_1806_02968_gb300 import api
+    out = {}
+    for fam, rows in PAPER_TABLES.items():
+        res = []
+        for key, cg_paper, rs_paper in rows:
+            if fam == "gaussian":
+                mat = W.gaussian_dense(key[0], key[1], 1)
+            elif fam == "semi_gaussian":
+                mat = W.semi_gaussian_dense(key[0], key[1], 1)
+            elif fam.startswith("udv"):
+                mat = W.udv_dense(90000, 300, float(np.sqrt(key)), 1, spacing="linear")
+            else:
+                mat = W.chung_lu_incidence(key, 5)
+            if mat["kind"] == "dense":
+                m, n = mat["A"].shape
+                A = torch.from_numpy(mat["A"]).cuda()
+                Mx, keep = api.Matrix(A), [A]
+            else:
+                m, n = mat["m"], mat["n"]
+                keep = [torch.from_numpy(mat[k]).cuda() for k in ("row_ptr", "col_idx", "vals")]
+                Mx = api.Matrix(row_ptr=keep[0], col_idx=keep[1], vals=keep[2], n=n)
+            B = torch.from_numpy(np.random.default_rng(1).standard_normal(m)).cuda()
+            row = {"m": m, "n": n, "iters_cg_paper": cg_paper, "iters_rs_paper": rs_paper}
+            for label, sweeps, seed_list in (("cg", 0, [1]), ("rs", 5, list(range(1, seeds + 1)))):
+                its, ms, rr, ok = [], [], [], []
+                for seed in seed_list:
+                    o = api.opts(seed=seed, sweeps=sweeps, tol=1e-7, max_outer=20)
+                    times = []
+                    for rep in range(warmup + steps):
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        idx, p, d = api.lsq_sample_rows(Mx, o)
+                        P = api.lsq_build_precond(Mx, idx, p, d, o)
+                        x, info = api.lsq_pcg_solve(Mx, P, B, o)
+                        torch.cuda.synchronize()
+                        if rep >= warmup:
+                            times.append(time.perf_counter() - t0)
+                    its.append(int(info.iters[0]))
+                    ms.append(1e3 * float(np.mean(times)))
+                    rr.append(float(info.relres_true[0]))
+                    ok.append(int(info.converged[0]))
+                    row["s"] = int(info.s)
+                row[f"iters_{label}"] = its if label == "rs" else its[0]
+                row[f"ms_{label}"] = float(np.mean(ms))
+                row[f"relres_true_{label}_max"] = max(rr)
+                row[f"converged_{label}"] = int(min(ok))
+            res.append(row)
+        out[fam] = res
+    return out
+
+
+def run_paper(args):
+    import torch
+    import paper_1806_02968_gb300 as pkg
+    pkg.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"metric": METRIC, "unit": "iterations; ms per solve (sampling + preconditioner + PCG)",
+                      "n_gpus": 1, "data": "synthetic", "dtype": "f64", "tol": 1e-7, "sweeps": 5,
+                      "tables": paper_tables(args.steps, args.warmup)}), flush=True)
+
+
 def run_tc(args):
     import torch
     import paper_1806_02968_gb300 as pkg
@@ -916,6 +1000,8 @@ def main():
         run_tc(args)
     elif args.workload == "sampling":
         run_sampling(args)
+    elif args.workload == "paper":
+        run_paper(args)
     elif args.workload not in ("udv", "gauss"):
         run_sparse_workload(args)
     else:

@@ -310,3 +310,47 @@ def test_sparse_block_persistent_matches_oracle(lsq, orc, case, k, sweeps):
         assert_iterations(info.iters[c], oi["iters"], _variants(orc, seen, smp, Mo, b[c], o),
                           f"persistent {case} t={sweeps} column {c}")
     assert all(info.converged[:k] == 1)
+
+
+def _components(mat):
+    """Connected-component label of every column of an incidence matrix (its null space of
+    B^T B is spanned by the indicator vectors of these components)."""
+    import scipy.sparse as sps
+    from scipy.sparse.csgraph import connected_components
+    B = sps.csr_matrix((mat["vals"], mat["col_idx"], mat["row_ptr"]), shape=(mat["m"], mat["n"]))
+    return connected_components(abs(B.T @ B), directed=False)[1]
+
+
+@pytest.mark.parametrize("n_param,sweeps,tol,k", [(96, 5, 1e-7, 1), (180, 5, 1e-7, 3), (96, 1, 1e-10, 3),
+                                                  (180, 1, 1e-10, 1)])
+def test_graph_laplacian_singular_matches_oracle(lsq, orc, n_param, sweeps, tol, k):
+    """The random graph Laplacian family of Sec. 5.5 at the paper's sizes (n = 187 and 355
+    vertices), with the paper's settings (t = 5, tolerance 1e-7) and the tight ones (t = 1,
+    1e-10).  B^T B is singular (one constant vector per connected component), so the normal
+    equations are consistent but x is unique only up to the null space: the fitted values,
+    the range part of x, the iteration counts and the convergence flags are compared."""
+    mat = W.chung_lu_incidence(n_param, 5)
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, mat, 31, sweeps=sweeps)
+    o.tol = tol
+    b = np.random.default_rng(n_param).standard_normal((k, seen["m"]))
+    X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b if k > 1 else b[0]).cuda(), o)
+    X = X.cpu().numpy().reshape(k, -1)
+    B = W.dense_from_csr(seen)
+    lab = _components(seen)
+    ev = np.linalg.eigvalsh((B / smp.d).T @ (B / smp.d))
+    kappa_eff = np.sqrt(ev[-1] / ev[ev > 1e-9 * ev[-1]][0])
+    for c in range(k):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=sweeps)
+        x_or = y / smp.d
+        assert info.converged[c] == 1 and oi["converged"] == 1
+        assert info.relres_true[c] <= tol
+        assert _same_solution(seen, smp.d, X[c], y, b[c], tol)
+        assert_iterations(info.iters[c], oi["iters"], _variants(orc, seen, smp, Mo, b[c], o),
+                          f"graph Laplacian n={seen['n']} t={sweeps} column {c}")
+        if tol <= 1e-10:
+            # the range part: x minus its mean over each component (D-weighted projections
+            # would do as well; the difference of two solutions is what is compared)
+            def rng_part(v):
+                return v - (np.bincount(lab, v) / np.bincount(lab))[lab]
+            assert_solution(B @ X[c], B @ x_or, kappa_eff, f"fitted values column {c}")
+            assert_solution(rng_part(X[c]), rng_part(x_or), kappa_eff, f"range part column {c}")

@@ -383,6 +383,30 @@ def test_pcg_matches_lapack_least_squares(orc, gen):
     assert np.linalg.norm(r) / np.linalg.norm(A.T @ b[0]) <= 1e-11
 
 
+def test_pcg_on_singular_graph_laplacian_gives_the_projection(orc):
+    """Sec. 5.5: for the incidence matrix B of a graph, B^T B is singular (one constant null
+    vector per connected component) but B^T B x = B^T b is consistent.  PCG then converges to
+    a solution whose fitted values B x are the orthogonal projection of b onto range(B), which
+    LAPACK's minimum-norm least-squares solution gives independently; the oracle's x may differ
+    from that one only by a per-component constant."""
+    mat = W.chung_lu_incidence(40, 3)
+    B = W.dense_from_csr(mat)
+    b = np.random.default_rng(2).standard_normal(mat["m"])
+    for sweeps in (1, 5):
+        S = orc.Solve(mat, b, seed=4, tol=1e-12, sweeps=sweeps)
+        assert S.info["converged"] == 1
+        x_mn, res, rank, sv = np.linalg.lstsq(B, b, rcond=None)
+        assert rank < mat["n"]                                        # really singular
+        kappa = sv[0] / sv[rank - 1]
+        fit = B @ x_mn
+        assert np.linalg.norm(B @ S.x - fit) / np.linalg.norm(fit) <= 10 * kappa ** 2 * 1e-12
+        # the difference lies in the null space: B (x - x_mn) = 0 up to the same bar, and
+        # x - x_mn is constant on each component
+        dx = S.x - x_mn
+        nul = sl.null_space(B)
+        assert np.linalg.norm(dx - nul @ (nul.T @ dx)) <= 10 * kappa ** 2 * 1e-12 * np.linalg.norm(x_mn)
+
+
 def test_pcg_energy_error_decreases_monotonically(orc):
     # CG minimises the A^T A-norm of the error over growing Krylov spaces.
     mat = W.udv_dense(400, 12, 1e2, 5)

@@ -67,3 +67,37 @@ def test_graph_incidence_rows_and_laplacian():
     # connected (the spanning path): the grounded Laplacian is nonsingular
     assert np.linalg.matrix_rank(full) == n_nodes - 1
     assert rows.size == mat["vals"].size
+
+
+def test_chung_lu_laplacian_family_sizes_and_structure():
+    """Sec. 5.5: B is the incidence matrix of two glued Chung-Lu graphs.  Each row holds +1 and
+    -1, B^T B = D - A (degrees on the diagonal, -1 per edge), isolated vertices are dropped and
+    the null space of B is the constant vector on each connected component.  The vertex count
+    for 2 n - 5 glued vertices and nnz(B^T B) = n + 2 m are the paper's printed sizes (its
+    table: n = 187, 355, 536, 709, 856; the number of edges is random, within 15 % of the
+    printed m = 5078 ... 101829)."""
+    paper = {96: (187, 5078), 180: (355, 19475), 270: (536, 41032), 357: (709, 68969),
+             430: (856, 101829)}
+    for n_param, (n_paper, m_paper) in paper.items():
+        mat = W.chung_lu_incidence(n_param, 5)
+        assert abs(mat["n"] - n_paper) <= 1, (mat["n"], n_paper)
+        assert abs(mat["m"] / m_paper - 1.0) < 0.16, (mat["m"], m_paper)
+    mat = W.chung_lu_incidence(96, 5)
+    B = W.dense_from_csr(mat)
+    m, n = B.shape
+    assert np.array_equal(np.sort(B, axis=1)[:, [0, -1]], np.tile([-1.0, 1.0], (m, 1)))
+    assert np.count_nonzero(B) == 2 * m
+    L = B.T @ B
+    deg = np.count_nonzero(B, axis=0)
+    assert deg.min() >= 1
+    np.testing.assert_array_equal(np.diag(L), deg)
+    off = L - np.diag(np.diag(L))
+    assert set(np.unique(off)) <= {-1.0, 0.0, -2.0}   # -2 only for an edge present in both graphs
+    np.testing.assert_array_equal(L.sum(axis=1), 0.0)
+    assert np.count_nonzero(L) == n + 2 * len({tuple(r) for r in np.argwhere(off != 0) if r[0] < r[1]})
+    # one null vector per component: rank n - (#components)
+    comps = int(np.sum(np.linalg.eigvalsh(L) < 1e-9 * n))
+    assert comps >= 1 and np.linalg.matrix_rank(B) == n - comps
+    g = W.chung_lu_incidence(96, 5, ground=True)
+    assert g["m"] == m and g["n"] == n - comps
+    assert np.linalg.matrix_rank(W.dense_from_csr(g)) == g["n"]

@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "gaussian_dense", "udv_dense", "semi_gaussian_dense", "coherent_dense",
-    "sparse_random", "graph_incidence", "rhs_for", "uneven_dense_batch",
+    "sparse_random", "graph_incidence", "chung_lu_incidence", "rhs_for", "uneven_dense_batch",
     "csr_from_dense", "dense_from_csr", "orthonormal_q",
 ]
 
@@ -188,6 +188,67 @@ def graph_incidence(n_nodes: int, n_edges: int, seed: int,
     vals = np.concatenate([sw, -sw])
     keep = cols != 0
     return _csr_from_coo(m, n_nodes - 1, rows[keep], cols[keep] - 1, vals[keep])
+
+
+def _chung_lu_edges(rng, n, beta, d, i0):
+    """Edges (i < j) of a Chung-Lu random graph with power-law expected degrees
+    w_i = c (i0 + i)^(-1/(beta-1)), c = (beta-2)/(beta-1) d n^(1/(beta-1)) (so that the mean
+    degree is about d); edge (i, j) present with probability min(1, w_i w_j / sum w)."""
+    c = (beta - 2.0) / (beta - 1.0) * d * n ** (1.0 / (beta - 1.0))
+    w = c * (i0 + np.arange(n, dtype=np.float64)) ** (-1.0 / (beta - 1.0))
+    P = np.minimum(1.0, np.outer(w, w) / w.sum())
+    upper = np.triu(rng.random((n, n)) < P, k=1)
+    return np.nonzero(upper)
+
+
+def chung_lu_incidence(n: int, seed: int, beta1: float = 5.0, d1: float = 30.0,
+                       beta2: float = 8.0, d2_per_node: float = 5.0, i0: int = 11,
+                       overlap: int = 5, ground: bool = False) -> dict:
+    """The random graph Laplacian family of Section 5.5: the incidence matrix B of a graph.
+
+    Two Chung-Lu power-law graphs on n vertices each: a sparse ill-conditioned one
+    (beta = 5, mean degree 30) and a dense well-conditioned one (beta = 8, mean degree 5 n,
+    capped by the edge probability 1), glued so that the last `overlap` vertices of the first
+    are the first of the second (2n - overlap vertices).  Every edge (i < j) is a row with +1
+    at i and -1 at j, so B^T B = D - A, the graph Laplacian.  Vertices without edges are
+    dropped.  B^T B is then singular (the constant vector of each connected component), as
+    in the paper, whose condition numbers for this family are the effective ones; the normal
+    equations stay consistent and the fitted values B x are unique.  With ground=True the
+    first vertex of every component is grounded (its column removed) instead, which gives
+    full column rank.
+    """
+    rng = _rng(seed)
+    s1, t1 = _chung_lu_edges(rng, n, beta1, d1, i0)
+    s2, t2 = _chung_lu_edges(rng, n, beta2, d2_per_node * n, i0)
+    off = n - overlap
+    src = np.concatenate([s1, s2 + off]).astype(np.int64)
+    dst = np.concatenate([t1, t2 + off]).astype(np.int64)
+    nv = 2 * n - overlap
+    used = np.zeros(nv, bool)
+    used[src] = True
+    used[dst] = True
+    # connected components (union-find over the edges): one grounded vertex each on request
+    parent = np.arange(nv)
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    for a, b in zip(src.tolist(), dst.tolist()):
+        ra, rb = find(a), find(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    roots = np.array([find(v) for v in range(nv)])
+    grounded = used & (roots == np.arange(nv)) if ground else np.zeros(nv, bool)
+    keep = used & ~grounded
+    col_of = -np.ones(nv, np.int64)
+    col_of[keep] = np.arange(int(keep.sum()))
+    m = src.size
+    rows = np.concatenate([np.arange(m), np.arange(m)])
+    cols = np.concatenate([col_of[src], col_of[dst]])
+    vals = np.concatenate([np.ones(m), -np.ones(m)])
+    ok = cols >= 0
+    return _csr_from_coo(m, int(keep.sum()), rows[ok], cols[ok], vals[ok])
 
 
 def rhs_for(mat: dict, k: int, noise: float, seed: int):

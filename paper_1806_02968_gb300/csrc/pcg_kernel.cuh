@@ -777,33 +777,12 @@ __device__ __forceinline__ bool row_pass(const PcgArgs& a, const void* vals, con
     return row_pass_rpw<DT, NMAX, MODE, 1>(a, vals, s_v, s_vc_raw, s_scal, r0, r1, ring, g);
 }
 
-// Grids of up to GRID_1RT CTAs read their per-CTA partials in ONE round of loads: every lane
-// issues all of its (predicated) loads before it adds any of them.  Larger grids loop.
-constexpr int GRID_1RT = 256;
-constexpr int NL_1RT = GRID_1RT / 32;
-// v[k] = base[(lane + 32 k) * stride] for lane + 32 k < G, else 0
-__device__ __forceinline__ void grid_load(const double* base, int64_t stride, int G, int lane, double (&v)[NL_1RT]) {
-#pragma unroll
-    for (int k = 0; k < NL_1RT; ++k) {
-        const int g = lane + 32 * k;
-        v[k] = g < G ? base[(int64_t)g * stride] : 0.0;
-    }
-}
-// the lane's part of a grid sum in a fixed pairwise order, then the warp sum
-__device__ __forceinline__ double grid_reduce(const double (&v)[NL_1RT]) {
-    return warp_sum(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
-}
-
 // sum_g part_s[g][slot] over all CTAs, computed by the calling warp (every warp of every
-// CTA sums in the same order, so all agree bit for bit); no block barrier.
+// CTA sums in the same order, so all agree bit for bit); no block barrier.  Four loads per
+// lane are in flight together.
 __device__ __forceinline__ double warp_grid_scalar(const PcgArgs& a, int slot) {
     const int lane = threadIdx.x & 31, G = (int)gridDim.x;
     const double* ps = a.part_s + slot;
-    if (G <= GRID_1RT) {
-        double v[NL_1RT];
-        grid_load(ps, PART_S, G, lane, v);
-        return grid_reduce(v);
-    }
     double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
     int g = lane;
     for (; g + 96 < G; g += 128) {
@@ -852,36 +831,25 @@ __device__ __forceinline__ void slice_reduce(const PcgArgs& a, int64_t c0, int64
 }
 
 // z_j = sum_k op_jk g_k for the owned rows (g staged in s_v); partial g^T z -> slot 2.
-template <typename OPT, int NMAX>
+template <typename OPT>
 __device__ __forceinline__ void op_rows(const PcgArgs& a, int64_t c0, int64_t c1,
                                         const double* s_v, double* s_scal) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const OPT* op = reinterpret_cast<const OPT*>(a.op);
     const int64_t n = a.n;
-    // a lane's entries of a row, NK at a time (the whole row at once for n <= 512): every
-    // load of a chunk is issued before any of its products
-    constexpr int NK = NMAX < 512 ? (NMAX + 31) / 32 : 16;
     double part = 0.0;
     for (int64_t j = c0 + wid; j < c1; j += nwarps) {
         const OPT* row = op + j * n;
         OPT t0 = OPT(0), t1 = OPT(0), t2 = OPT(0), t3 = OPT(0);
-        for (int64_t k0 = 0; k0 < n; k0 += 32 * NK) {
-            OPT r[NK];
-#pragma unroll
-            for (int q = 0; q < NK; ++q) {
-                const int64_t k = k0 + lane + 32 * q;
-                r[q] = k < n ? row[k] : OPT(0);
-            }
-#pragma unroll
-            for (int q = 0; q < NK; ++q) {
-                const int64_t k = k0 + lane + 32 * q;
-                const OPT sv = k < n ? (OPT)s_v[k] : OPT(0);
-                if ((q & 3) == 0) t0 = fma(r[q], sv, t0);
-                else if ((q & 3) == 1) t1 = fma(r[q], sv, t1);
-                else if ((q & 3) == 2) t2 = fma(r[q], sv, t2);
-                else t3 = fma(r[q], sv, t3);
-            }
+        int64_t k = lane;
+#pragma unroll 4
+        for (; k + 96 < n; k += 128) {
+            t0 = fma(row[k], (OPT)s_v[k], t0);
+            t1 = fma(row[k + 32], (OPT)s_v[k + 32], t1);
+            t2 = fma(row[k + 64], (OPT)s_v[k + 64], t2);
+            t3 = fma(row[k + 96], (OPT)s_v[k + 96], t3);
         }
+        for (; k < n; k += 32) t0 = fma(row[k], (OPT)s_v[k], t0);
         const double zj = (double)warp_sum((t0 + t1) + (t2 + t3));
         if (lane == 0) {
             a.z[j] = zj;
@@ -908,35 +876,26 @@ __device__ __forceinline__ bool step_update(const PcgArgs& a, int64_t c0, int64_
     if (own && lane == 0) { yj = a.y[j0]; gj = a.g[j0]; }
     const double* ps = a.part_s;
     const double* pw = a.part_w + (own ? j0 : 0);
-    double pTw, wsum;
-    if (G <= GRID_1RT) {
-        double t[NL_1RT], u[NL_1RT];
-        grid_load(ps, PART_S, G, lane, t);
-        grid_load(pw, n, own ? G : 0, lane, u);
-        pTw = grid_reduce(t);
-        wsum = grid_reduce(u);
-    } else {
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
-        int g = lane;
-        for (; g + 96 < G; g += 128) {
-            t0 += ps[(int64_t)g * PART_S];
-            t1 += ps[(int64_t)(g + 32) * PART_S];
-            t2 += ps[(int64_t)(g + 64) * PART_S];
-            t3 += ps[(int64_t)(g + 96) * PART_S];
-            if (own) {
-                u0 += pw[(int64_t)g * n];
-                u1 += pw[(int64_t)(g + 32) * n];
-                u2 += pw[(int64_t)(g + 64) * n];
-                u3 += pw[(int64_t)(g + 96) * n];
-            }
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+    int g = lane;
+    for (; g + 96 < G; g += 128) {
+        t0 += ps[(int64_t)g * PART_S];
+        t1 += ps[(int64_t)(g + 32) * PART_S];
+        t2 += ps[(int64_t)(g + 64) * PART_S];
+        t3 += ps[(int64_t)(g + 96) * PART_S];
+        if (own) {
+            u0 += pw[(int64_t)g * n];
+            u1 += pw[(int64_t)(g + 32) * n];
+            u2 += pw[(int64_t)(g + 64) * n];
+            u3 += pw[(int64_t)(g + 96) * n];
         }
-        for (; g < G; g += 32) {
-            t0 += ps[(int64_t)g * PART_S];
-            if (own) u0 += pw[(int64_t)g * n];
-        }
-        pTw = warp_sum((t0 + t1) + (t2 + t3));
-        wsum = warp_sum((u0 + u1) + (u2 + u3));
     }
+    for (; g < G; g += 32) {
+        t0 += ps[(int64_t)g * PART_S];
+        if (own) u0 += pw[(int64_t)g * n];
+    }
+    const double pTw = warp_sum((t0 + t1) + (t2 + t3));
+    const double wsum = warp_sum((u0 + u1) + (u2 + u3));
     if (!(pTw > 0.0) || !(rho > 0.0) || !isfinite(pTw) || !isfinite(rho)) return false;
     const double alpha = rho / pTw;
     double part = 0.0;
@@ -1086,7 +1045,7 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
             // z = P g, rho = g^T z, p = z
             for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s_v[j] = a.g[j];
             __syncthreads();
-            op_rows<OPT, NMAX>(a, c0, c1, s_v, s_scal);
+            op_rows<OPT>(a, c0, c1, s_v, s_scal);
             LSQ_BARRIER();
             double rho = warp_grid_scalar(a, 2);
             for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
@@ -1112,7 +1071,7 @@ __global__ void __launch_bounds__(512, 1) k_pcg_dense(PcgArgs a) {
                 __syncthreads();
                 if (rec <= a.tol || sqrt(gg) <= a.inner_tol * gstart) break;
                 if (iters >= a.maxit) break;
-                op_rows<OPT, NMAX>(a, c0, c1, s_v, s_scal);
+                op_rows<OPT>(a, c0, c1, s_v, s_scal);
                 LSQ_BARRIER();
                 {
                     // rho' = g^T z over the grid and p = z + beta p; z's loads go out first

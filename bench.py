@@ -58,6 +58,8 @@ def parse():
                     help="udv: the timed benchmark; the others measure one other configuration alone")
     ap.add_argument("--device-loop", type=int, default=0,
                     help="CSR blocks of right-hand sides: 1 = one persistent launch per solve")
+    ap.add_argument("--sweep-form", type=int, default=0,
+                    help="one-column sparse sweeps: 0 by shape, 1 grid, 2 one CTA, 3 one cluster")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations and the FP64 comparison solve after the timed region")
     return ap.parse_args()
@@ -641,8 +643,10 @@ def sparse_config(which, tol=1e-10, maxit=1000000, sweeps=1, inner_tol=0.0, step
 def run_sparse_workload(args):
     import torch
     import paper_1806_02968_gb300 as pkg
+    from paper_1806_02968_gb300 import api
     pkg.build()
     torch.cuda.set_device(0)
+    api.set_sweep_form(args.sweep_form)
     out = sparse_config(args.workload, args.tol, args.maxit, args.sweeps, args.inner_tol,
                         args.steps, args.warmup, cpu=not args.no_cpu_baseline, device_loop=args.device_loop)
     line = {"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", **out}
@@ -934,8 +938,10 @@ def paper_tables(steps=1, warmup=1, seeds=5):
                 mat = W.chung_lu_incidence(key, 5)
             if mat["kind"] == "dense":
                 m, n = mat["A"].shape
-                A = torch.from_numpy(mat["A"]).cuda()
-                Mx, keep = api.Matrix(A), [A]
+                # rows start on 16-byte boundaries (the row copies' alignment): pad odd n
+                A = torch.zeros(m, n + (n & 1), dtype=torch.float64, device="cuda")
+                A[:, :n] = torch.from_numpy(mat["A"]).cuda()
+                Mx, keep = api.Matrix(A[:, :n]), [A]
             else:
                 m, n = mat["m"], mat["n"]
                 keep = [torch.from_numpy(mat[k]).cuda() for k in ("row_ptr", "col_idx", "vals")]

@@ -395,6 +395,21 @@ LSQ_API int64_t lsq_kernel_launch_count(void);
  * 0 <= max_polls <= 2^31. */
 LSQ_API lsq_status lsq_set_wait_limit(int64_t max_polls);
 
+/* Form of the one-column sparse Gauss-Seidel sweeps (Alg. 3 on a CSR A_s^T A_s), a tuning and
+ * test setting; every form computes the same rows in the same level order with the same
+ * per-row arithmetic:
+ *   0  chosen from the level schedule's shape: one CTA or the grid (the default),
+ *   1  the grid: every row waits (bounded) for the values of its own dependencies,
+ *   2  one CTA: levels meet at block barriers,
+ *   3  one thread-block cluster of 8 CTAs: the sweep vector in the cluster's shared memory
+ *      and levels at cluster barriers; where it does not fit (n > 204,800 or no cluster slot
+ *      on the device) the grid form runs instead.
+ * Blocks of k >= 2 right-hand sides (stream-ordered solves) take form 3 as well, where their
+ * n x k vector fits (n k <= 204,800); every other value leaves them on their grid forms.
+ * Process-wide, read when a solve or preconditioner application starts.  LSQ_ERR_INVALID
+ * unless 0 <= form <= 3. */
+LSQ_API lsq_status lsq_set_sweep_form(int32_t form);
+
 #ifdef __cplusplus
 }
 #endif

@@ -334,6 +334,11 @@ def set_wait_limit(max_polls: int = 0):
     _check(L.load().lsq_set_wait_limit(int(max_polls)), "lsq_set_wait_limit")
 
 
+def set_sweep_form(form: int = 0):
+    """Form of the one-column sparse sweeps: 0 by shape, 1 grid, 2 one CTA, 3 one cluster."""
+    _check(L.load().lsq_set_sweep_form(int(form)), "lsq_set_sweep_form")
+
+
 def solve(A: Matrix, b, o=None, stream=None):
     """Alg. 2 end to end: sample, build the preconditioner, PCG. Returns (x, Info, extras)."""
     o = o or opts()

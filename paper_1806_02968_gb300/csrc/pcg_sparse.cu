@@ -16,6 +16,8 @@
 #include "sparse.cuh"
 #include "values.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 namespace lsq {
@@ -50,6 +52,8 @@ struct SpArgs {
     const int64_t* loff_f;      // first slot of each level
     const int64_t* loff_b;
     int64_t one_f, one_b;       // level count when that direction runs in one CTA, else 0
+    int64_t cl_f, cl_b;         // level count when that direction runs in one cluster, else 0
+    int cl_lg;                  // log2 of that cluster's size
     int lpr, lpc;               // lanes per row of A, lanes per column of A (powers of two <= 32)
     int sweeps;
     // vectors
@@ -188,6 +192,9 @@ constexpr int SW_PF = 16;           // dependency entries per lane held in regis
 // and read back between levels.  Warp w takes schedule slots w, w + W, ... (rows sorted by
 // level), all warps resident, so every wait ends.
 constexpr unsigned long long SWEEP_EMPTY = 0xFFF7DEADBEEFCAFEull;
+constexpr int SWG = 8;                 // dependency values a lane loads before it polls
+constexpr unsigned SW_SPIN = 4;        // polls before the first back-off
+constexpr unsigned SW_NS_CAP = 256;    // longest back-off between polls (ns)
 __global__ void k_fill_empty(double* e, int64_t n) {
     unsigned long long* u = reinterpret_cast<unsigned long long*>(e);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -227,32 +234,32 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool other = !identity && e_old != nullptr;
     bool ok = true;
-    // the values of up to 8 dependencies per lane: issue all loads, then poll the missing
-    auto gather8 = [&](const int32_t (&kk)[8], const double (&mm)[8], double& acc) {
-        unsigned long long u[8];
+    // the values of up to SWG dependencies per lane: issue all loads, then poll the missing
+    auto gather = [&](const int32_t (&kk)[SWG], const double (&mm)[SWG], double& acc) {
+        unsigned long long u[SWG];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) u[c] = kk[c] >= 0 ? ld_volatile_u64(e_new + kk[c]) : 0ull;
+        for (int c = 0; c < SWG; ++c) u[c] = kk[c] >= 0 ? ld_volatile_u64(e_new + kk[c]) : 0ull;
         unsigned polls = 0, ns = 32;
         while (true) {
             bool missing = false;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) missing = missing || (kk[c] >= 0 && u[c] == SWEEP_EMPTY);
+            for (int c = 0; c < SWG; ++c) missing = missing || (kk[c] >= 0 && u[c] == SWEEP_EMPTY);
             if (!missing) break;
             ++polls;
             if (polls > a.max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
                 ok = false;
                 atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) if (u[c] == SWEEP_EMPTY) u[c] = 0ull;
+                for (int c = 0; c < SWG; ++c) if (u[c] == SWEEP_EMPTY) u[c] = 0ull;
                 break;
             }
-            if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }
+            if (polls > SW_SPIN) { __nanosleep(ns); ns = ns < SW_NS_CAP ? 2 * ns : SW_NS_CAP; }
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < SWG; ++c)
                 if (kk[c] >= 0 && u[c] == SWEEP_EMPTY) u[c] = ld_volatile_u64(e_new + kk[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int c = 0; c < SWG; ++c)
             if (kk[c] >= 0) acc = fma(mm[c], __longlong_as_double((long long)u[c]), acc);
     };
     for (int64_t slot = gw; slot < a.n; slot += W) {
@@ -265,17 +272,17 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
             for (int64_t e = o0 + lane; e < o1; e += 32) acc = fma((double)mv[e], e_old[a.mcol[e]], acc);
         const double base = identity ? e_old[j] : r[j];
         const double dj = a.dinv[j];
-        for (int64_t b0 = d0 + lane; b0 < d1; b0 += 32 * 8) {
-            int32_t kk[8];
-            double mm[8];
+        for (int64_t b0 = d0 + lane; b0 < d1; b0 += 32 * SWG) {
+            int32_t kk[SWG];
+            double mm[SWG];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < SWG; ++c) {
                 const int64_t e = b0 + 32 * c;
                 kk[c] = -1;
                 mm[c] = 0.0;
                 if (e < d1) { kk[c] = a.mcol[e]; mm[c] = (double)mv[e]; }
             }
-            gather8(kk, mm, acc);
+            gather(kk, mm, acc);
         }
         acc = warp_sum(acc);
         if (lane == 0) {
@@ -389,6 +396,130 @@ __global__ void __launch_bounds__(S1_T, 1) k_sp_sweep_1cta(SpArgs a, const doubl
     }
 }
 
+// The same sweep in ONE thread-block cluster of C = 2^lg CTAs, for deep level structures
+// whose levels are too wide for one SM but whose sweep vector fits in the cluster's shared
+// memory.  e_new_j lives in the shared memory of CTA (j mod C) at slot j / C; a row's
+// gathers read its owners' shared memory (DSMEM) and the levels meet at hardware cluster
+// barriers, so no value makes a round trip through L2 and nothing is polled.  Warp w of CTA
+// r takes rows w C + r, w C + r + C NW, ... of each level; its first row of the next level
+// (indices, values, and the terms that do not depend on this sweep) is loaded before the
+// barrier, as in the one-CTA form.  Every value is also stored to e_new in global memory
+// for the kernels that follow.
+constexpr int SC_T = 512;
+template <typename MT, bool FWD>
+__global__ void __launch_bounds__(SC_T, 1) k_sp_sweep_cl(SpArgs a, const double* r, const double* e_old,
+                                                         double* e_new, int identity, int check, int nparts,
+                                                         int64_t nlev, int lg) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) double xs[];   // this CTA's slots of e_new
+    __shared__ double sh[40];
+    __shared__ int s_stop;
+    // Every CTA takes the same exits before the first cluster barrier: done is only written
+    // by this launch's check (rank 0), whose decision every CTA computes identically.
+    if (a.S->done) return;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned C = 1u << lg, me = cl.block_rank();
+    if (check) {
+        const double gg = sum_parts(a.part + a.rblk, nparts, sh);
+        if (threadIdx.x == 0) {
+            const double gn = sqrt(gg);
+            int stop = 0;
+            if (gn <= a.tol * a.S->hn || gn <= a.inner_tol * a.S->gstart) stop = 1;
+            if (a.S->iters >= a.maxit) stop = 1;
+            s_stop = stop;
+            if (me == 0) {
+                a.S->rec = gn / a.S->hn;
+                if (stop) a.S->done = 1;
+            }
+        }
+        __syncthreads();
+        if (s_stop) return;
+    }
+    const int32_t* sched = FWD ? a.sched_f : a.sched_b;
+    const int64_t* loff = FWD ? a.loff_f : a.loff_b;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int NW = (int)(blockDim.x >> 5);
+    const int64_t gw = (int64_t)w * C + me, GW = (int64_t)NW * C;
+    const unsigned cmask = C - 1u;
+    const bool other = !identity && e_old != nullptr;
+    struct Row {
+        int64_t j, d0, d1;
+        double base, acc;
+        int32_t kk[SW_PF];
+        MT mm[SW_PF];
+    };
+    auto load_row = [&](int64_t j, Row& R) {
+        R.j = j;
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        R.d0 = FWD ? e0 : ed + 1;
+        R.d1 = FWD ? ed : e1;
+        const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
+        R.base = identity ? e_old[j] : r[j];
+        R.acc = 0.0;
+        if (other)
+            for (int64_t e = o0 + lane; e < o1; e += 32) R.acc = fma((double)mv[e], e_old[a.mcol[e]], R.acc);
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c) {
+            const int64_t e = R.d0 + lane + 32 * c;
+            R.kk[c] = -1;
+            R.mm[c] = MT(0);
+            if (e < R.d1) { R.kk[c] = a.mcol[e]; R.mm[c] = mv[e]; }
+        }
+    };
+    auto gather = [&](int32_t k) -> double {
+        const double* src = cl.map_shared_rank(xs, (unsigned)k & cmask);
+        return src[(unsigned)k >> lg];
+    };
+    auto finish_row = [&](const Row& R) {
+        double v[SW_PF];
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c) v[c] = R.kk[c] >= 0 ? gather(R.kk[c]) : 0.0;
+        double acc = R.acc;
+#pragma unroll
+        for (int c = 0; c < SW_PF; ++c) acc = fma((double)R.mm[c], v[c], acc);
+        for (int64_t b0 = R.d0 + 32 * SW_PF; b0 < R.d1; b0 += 32 * 8) {
+            int32_t k2[8];
+            double m2[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t e = b0 + lane + 32 * u;
+                k2[u] = -1;
+                m2[u] = 0.0;
+                if (e < R.d1) { k2[u] = a.mcol[e]; m2[u] = (double)mv[e]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k2[u] >= 0) acc = fma(m2[u], gather(k2[u]), acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double dj = a.dinv[R.j];
+            const double val = identity ? R.base - acc * dj : (R.base - acc) * dj;
+            double* dst = cl.map_shared_rank(xs, (unsigned)R.j & cmask);
+            dst[(unsigned)R.j >> lg] = val;
+            e_new[R.j] = val;
+        }
+    };
+    Row cur;
+    int64_t lo = loff[0], hi = loff[1];
+    if (gw < hi - lo) load_row(sched[lo + gw], cur);
+    cl.sync();   // every CTA of the cluster runs before any shared memory is read remotely
+    for (int64_t L = 0; L < nlev; ++L) {
+        const int64_t cnt = hi - lo;
+        for (int64_t q = gw; q < cnt; q += GW) {
+            if (q != gw) load_row(sched[lo + q], cur);
+            finish_row(cur);
+        }
+        if (L + 1 < nlev) {
+            lo = hi;
+            hi = loff[L + 2];
+            if (gw < hi - lo) load_row(sched[lo + gw], cur);
+        }
+        cl.sync();   // this level's values are visible in every CTA; after the last, no CTA reads another's memory
+    }
+}
+
 // t = 0 (the comparison method, P = I): z = g, with the convergence check of the first sweep
 __global__ void __launch_bounds__(SP_T) k_sp_identity(SpArgs a, const double* r, double* e, int check, int nparts) {
     __shared__ double sh[40];
@@ -484,8 +615,60 @@ __global__ void k_gather_pairs(const float* src, const int64_t* perm, int64_t nn
     }
 }
 
+// The cluster form's size (8 CTAs, the portable maximum) and its shared-memory budget per CTA.
+constexpr int SC_LG = 3;
+constexpr int64_t SC_SMEM = 200 * 1024;
+// Sweep form override (lsq_set_sweep_form): 0 chosen by shape, 1 grid, 2 one CTA, 3 one cluster.
+static std::atomic<int> g_sweep_form{0};
+int sweep_form_setting() { return g_sweep_form.load(std::memory_order_relaxed); }
+
+// Launch of the cluster form; false (nothing launched) when the cluster does not fit.
+template <typename MT, bool FWD>
+static bool launch_sweep_cluster(const SpArgs& a, const double* r, const double* eold, double* enew,
+                                 int identity, int check, int nparts, int64_t nl, cudaStream_t st,
+                                 lsq_status& status) {
+    static std::atomic<int> fits{-1};   // per kernel instance: the cluster fits on this device
+    auto kern = k_sp_sweep_cl<MT, FWD>;
+    const int C = 1 << SC_LG;
+    const size_t smem = (size_t)8 * (size_t)((a.n + C - 1) / C);
+    if ((int64_t)smem > SC_SMEM) return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(SC_T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int f = fits.load(std::memory_order_relaxed);
+    if (f < 0) {
+        f = 0;
+        if (cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t probe = cfg;
+            probe.dynamicSmemBytes = SC_SMEM;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)kern, &probe) == cudaSuccess && clusters > 0)
+                f = 1;
+        }
+        cudaGetLastError();   // a refused query leaves the grid form in use, not an error
+        fits.store(f, std::memory_order_relaxed);
+    }
+    if (!f) return false;
+    const int lg = SC_LG;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, r, eold, enew, identity, check, nparts, nl, lg);
+    count_launch();
+    status = e == cudaSuccess ? LSQ_OK : LSQ_ERR_CUDA;
+    if (e != cudaSuccess) set_error(std::string("cluster sweep launch: ") + cudaGetErrorString(e));
+    return true;
+}
+
 // Cooperative launch of a sweep with one co-resident grid (every warp must run at once for
-// the level waits to end).
+// the level waits to end), or the one-CTA or one-cluster form when the schedule calls for it.
 template <typename MT, bool FWD>
 static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* eold, double* enew,
                                int identity, int check, int nparts, int idx, cudaStream_t st) {
@@ -508,6 +691,11 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
         LSQ_CUDA(cudaGetLastError());
         return LSQ_OK;
     }
+    const int64_t ncl = FWD ? a.cl_f : a.cl_b;
+    if (ncl > 0) {   // deep levels of moderate width, the vector within a cluster's shared memory
+        lsq_status q = LSQ_OK;
+        if (launch_sweep_cluster<MT, FWD>(a, r, eold, enew, identity, check, nparts, ncl, st, q)) return q;
+    }
     // the grid form: fill e_new with the empty marker, then the value-flag sweep
     k_fill_empty<<<(unsigned)std::min<int64_t>((a.n + SP_T - 1) / SP_T, 152 * 8), SP_T, 0, st>>>(enew, a.n);
     count_launch();
@@ -519,14 +707,27 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
     return LSQ_OK;
 }
 
-// One CTA per sweep when a level holds fewer than 2048 dependency entries on average: block
-// barriers between levels are then cheaper than a grid of warps polling for the values they
-// depend on, and one SM's loads still keep up with a level's gathers (at ~10,000 entries per
-// level one SM is twice slower than the grid).
+// The sweep form of each direction.  By shape (form 0): one CTA when a level holds fewer than
+// 2048 dependency entries on average: block barriers between levels are then cheaper than a
+// grid of warps polling for the values they depend on, and one SM's loads still keep up with
+// a level's gathers (at ~10,000 entries per level one SM is twice slower than the grid);
+// otherwise the grid.  The cluster form is never chosen by shape: on the 4e6 x 4e4 workload
+// (1583 levels of ~9,600 dependency entries) it took 8.0 ms per sweep against the grid's 5.8,
+// because a cluster barrier's release waits for the next level's row loads still in flight
+// and random gathers from other CTAs' shared memory are throughput-limited per SM.
 static void choose_sweep_form(SpArgs& a, const SparseHandle* SH, int64_t n) {
     const double dep = 0.5 * (double)(SH->nnz_M - n);   // dependency entries per direction
-    a.one_f = dep < 2048.0 * (double)SH->nlev_f ? SH->nlev_f : 0;
-    a.one_b = dep < 2048.0 * (double)SH->nlev_b ? SH->nlev_b : 0;
+    const int form = g_sweep_form.load(std::memory_order_relaxed);
+    const bool fits = 8 * ((n + (1 << SC_LG) - 1) >> SC_LG) <= SC_SMEM;
+    a.cl_lg = SC_LG;
+    auto pick = [&](int64_t nlev, int64_t& one, int64_t& clv) {
+        one = clv = 0;
+        if (form == 2) one = nlev;
+        else if (form == 3) clv = fits ? nlev : 0;
+        else if (form == 0 && dep < 2048.0 * (double)nlev) one = nlev;
+    };
+    pick(SH->nlev_f, a.one_f, a.cl_f);
+    pick(SH->nlev_b, a.one_b, a.cl_b);
 }
 
 static unsigned gridn(int64_t work, int64_t cap = 152 * 8) {
@@ -924,3 +1125,12 @@ lsq_status sparse_solve(const lsq_matrix* A, const lsq_precond* P, const double*
 }
 
 }  // namespace lsq
+
+extern "C" lsq_status lsq_set_sweep_form(int32_t form) {
+    if (form < 0 || form > 3) {
+        lsq::set_error("lsq_set_sweep_form: form must be 0, 1, 2 or 3");
+        return LSQ_ERR_INVALID;
+    }
+    lsq::g_sweep_form.store(form, std::memory_order_relaxed);
+    return LSQ_OK;
+}

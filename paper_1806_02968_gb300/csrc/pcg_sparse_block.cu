@@ -23,6 +23,8 @@
 #include "bk_device.cuh"
 #include "sparse_persist.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -70,6 +72,115 @@ __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r
                                                        double* e_new, int identity, int sweep_idx) {
     if (a.S->done) return;
     bk_sweep_cta_body<MT, FWD, KT>(a, r, e_old, e_new, identity, sweep_idx);
+}
+
+// The CTA-per-row sweep in ONE thread-block cluster of C = 2^lg CTAs, for deep level
+// structures whose block vector (n x K) fits in the cluster's shared memory.  Row j's K values
+// live in CTA (j mod C) at slots (j / C) K ... (j / C) K + K - 1.  CTA r takes rows r, r + C,
+// ... of each level, and its threads take a row's dependency entries as in the CTA form
+// (thread t: entries t, t + BK_T, ..., the same order, so the same sums); the gathers read the
+// owners' shared memory (DSMEM) and the levels meet at cluster barriers, so nothing is
+// polled.  The CTA's first row of the next level (its indices and values) is loaded before
+// the barrier.  Every value is also stored to e_new in global memory.
+template <typename MT, bool FWD, int KT>
+__global__ void __launch_bounds__(BK_T, 1) k_bk_sweep_cl(BkArgs a, const double* r, const double* e_old,
+                                                         double* e_new, int identity, const int64_t* loff,
+                                                         int64_t nlev, int lg) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) double xs[];   // this CTA's rows of e_new, K values each
+    __shared__ double s_part[BK_T / 32][KT];
+    // the same exit in every CTA: done only changes in the update step, not during a sweep
+    if (a.S->done) return;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned C = 1u << lg, me = cl.block_rank(), cmask = C - 1u;
+    const int32_t* sched = FWD ? a.sched_f : a.sched_b;
+    const MT* mv = reinterpret_cast<const MT*>(a.mval);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int K = a.K;
+    const bool other = !identity && e_old != nullptr;
+    constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
+    constexpr int PF = 2;   // dependency entries per thread loaded ahead (rows up to 2 BK_T entries)
+    struct Row {
+        int64_t j, d0, d1;
+        int32_t kk[PF];
+        MT mm[PF];
+    };
+    auto load_row = [&](int64_t j, Row& R) {
+        R.j = j;
+        const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+        R.d0 = FWD ? e0 : ed + 1;
+        R.d1 = FWD ? ed : e1;
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int64_t e = R.d0 + tid + (int64_t)BK_T * u;
+            R.kk[u] = -1;
+            R.mm[u] = MT(0);
+            if (e < R.d1) { R.kk[u] = a.mcol[e]; R.mm[u] = mv[e]; }
+        }
+    };
+    auto entry = [&](int32_t k, double mk, double (&acc)[KT]) {
+        const double* src = cl.map_shared_rank(xs, (unsigned)k & cmask) + (int64_t)((unsigned)k >> lg) * K;
+        double v[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) v[c] = c < K ? src[c] : 0.0;
+#pragma unroll
+        for (int c = 0; c < KT; ++c)
+            if (c < K) acc[c] = fma(mk, v[c], acc[c]);
+    };
+    auto finish_row = [&](const Row& R) {
+        const int64_t j = R.j;
+        double acc[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) acc[c] = 0.0;
+        if (other) {
+            const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
+            const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
+            for (int64_t e = o0 + tid; e < o1; e += BK_T) {
+                const int64_t k = a.mcol[e];
+                const double mk = (double)mv[e];
+#pragma unroll
+                for (int c = 0; c < KT; ++c)
+                    if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (R.kk[u] >= 0) entry(R.kk[u], (double)R.mm[u], acc);
+        for (int64_t e = R.d0 + tid + (int64_t)BK_T * PF; e < R.d1; e += BK_T)
+            entry(a.mcol[e], (double)mv[e], acc);
+        const double tot = bk_reduce_scatter<KT>(acc, lane);
+        if ((lane & ((1 << SH) - 1)) == 0) s_part[wid][lane >> SH] = tot;
+        __syncthreads();
+        if (wid == 0 && lane < K) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][lane];
+            const double dj = a.dinv[j];
+            const int64_t at = j * K + lane;
+            const double val = identity ? e_old[at] - sum * dj : (r[at] - sum) * dj;
+            double* dst = cl.map_shared_rank(xs, (unsigned)j & cmask) + (int64_t)((unsigned)j >> lg) * K;
+            dst[lane] = val;
+            e_new[at] = val;
+        }
+        __syncthreads();   // s_part is reused by the next row
+    };
+    Row cur;
+    int64_t lo = loff[0], hi = loff[1];
+    if ((int64_t)me < hi - lo) load_row(sched[lo + me], cur);
+    cl.sync();   // every CTA of the cluster runs before any shared memory is read remotely
+    for (int64_t L = 0; L < nlev; ++L) {
+        const int64_t cnt = hi - lo;
+        for (int64_t q = me; q < cnt; q += C) {
+            if (q != (int64_t)me) load_row(sched[lo + q], cur);
+            finish_row(cur);
+        }
+        if (L + 1 < nlev) {
+            lo = hi;
+            hi = loff[L + 2];
+            if ((int64_t)me < hi - lo) load_row(sched[lo + me], cur);
+        }
+        cl.sync();   // this level's values are visible in every CTA; after the last, no CTA reads another's memory
+    }
 }
 
 __global__ void __launch_bounds__(BK_T) k_bk_gz(BkArgs a, int first) {
@@ -178,6 +289,71 @@ static const void* bk_sweep_kernel(int mode, int K) {
     return (const void*)k_bk_sweep_cta<MT, FWD, 32>;
 }
 
+template <typename MT, bool FWD>
+static const void* bk_sweep_cl_kernel(int K) {
+    if (K <= 2) return (const void*)k_bk_sweep_cl<MT, FWD, 2>;
+    if (K <= 4) return (const void*)k_bk_sweep_cl<MT, FWD, 4>;
+    if (K <= 8) return (const void*)k_bk_sweep_cl<MT, FWD, 8>;
+    if (K <= 16) return (const void*)k_bk_sweep_cl<MT, FWD, 16>;
+    return (const void*)k_bk_sweep_cl<MT, FWD, 32>;
+}
+
+// The cluster form's size (8 CTAs, the portable maximum) and shared-memory budget per CTA.
+constexpr int BC_LG = 3;
+constexpr int64_t BC_SMEM = 200 * 1024;
+static int64_t bk_cl_smem(int64_t n, int K) { return 8 * K * ((n + (1 << BC_LG) - 1) >> BC_LG); }
+
+// True when the cluster form of this kernel can run on this device (once per kernel).
+static bool bk_cluster_fits(const void* kern) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, bool> ok;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = ok.find(kern);
+    if (it != ok.end()) return it->second;
+    bool f = false;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BC_SMEM) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1 << BC_LG;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(1 << BC_LG);
+        cfg.blockDim = dim3(BK_T);
+        cfg.dynamicSmemBytes = BC_SMEM;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        f = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0;
+    }
+    cudaGetLastError();   // a refused query leaves the grid forms in use, not an error
+    ok[kern] = f;
+    return f;
+}
+
+static lsq_status bk_launch_sweep_cl(const void* kern, const BkArgs& a, const double* r, const double* eold,
+                                     double* enew, int identity, const int64_t* loff, int64_t nlev,
+                                     cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1 << BC_LG;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(1 << BC_LG);
+    cfg.blockDim = dim3(BK_T);
+    cfg.dynamicSmemBytes = (size_t)bk_cl_smem(a.n, a.K);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BkArgs av = a;
+    int lg = BC_LG;
+    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, (void*)&loff, &nlev, &lg};
+    LSQ_CUDA(cudaLaunchKernelExC(&cfg, kern, params));
+    count_launch();
+    return LSQ_OK;
+}
+
 struct BkOut {
     int32_t iters[BK_MAX], outer[BK_MAX];
     uint8_t conv[BK_MAX];
@@ -266,9 +442,26 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     const bool m32 = P->op_dtype == LSQ_F32;
     const void* kf = m32 ? bk_sweep_kernel<float, true>(smode, K) : bk_sweep_kernel<double, true>(smode, K);
     const void* kb = m32 ? bk_sweep_kernel<float, false>(smode, K) : bk_sweep_kernel<double, false>(smode, K);
+    // one cluster on request (lsq_set_sweep_form 3) where the block vector fits in the
+    // cluster's shared memory; the stream-ordered solve only (the persistent kernel keeps the
+    // grid forms).  Never chosen by shape: on the 1e6 x 1e4 workload with 16 columns (1227
+    // levels of ~8 rows with ~350 dependency entries) the solve took 686 ms against 395 ms with
+    // the CTA-per-row grid form.
+    const int form = sweep_form_setting();
+    const void* cf = m32 ? bk_sweep_cl_kernel<float, true>(K) : bk_sweep_cl_kernel<double, true>(K);
+    const void* cb = m32 ? bk_sweep_cl_kernel<float, false>(K) : bk_sweep_cl_kernel<double, false>(K);
+    auto want_cl = [&](int64_t nlev) {
+        (void)nlev;
+        return form == 3 && bk_cl_smem(n, K) <= BC_SMEM;
+    };
+    const bool cl_f = want_cl(SH->nlev_f) && bk_cluster_fits(cf);
+    const bool cl_b = want_cl(SH->nlev_b) && bk_cluster_fits(cb);
     lsq_status sweep_status = LSQ_OK;
     auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int idx) {
-        lsq_status q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, st);
+        lsq_status q;
+        if (fwd && cl_f) q = bk_launch_sweep_cl(cf, a, r, eold, enew, identity, SH->loff_f, SH->nlev_f, st);
+        else if (!fwd && cl_b) q = bk_launch_sweep_cl(cb, a, r, eold, enew, identity, SH->loff_b, SH->nlev_b, st);
+        else q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, st);
         if (q != LSQ_OK) sweep_status = q;
     };
     // z = P g: t forward then t backward sweeps

@@ -31,6 +31,8 @@ lsq_status transpose_pattern(const int64_t* rptr, const int32_t* col, int64_t nr
 lsq_status build_sparse(const lsq_matrix* A, const int32_t* idx, const double* p, int64_t s,
                         lsq_precond* H, cudaStream_t st);
 void free_sparse(SparseHandle* S);
+// The sweep form set by lsq_set_sweep_form (0 by shape, 1 grid, 2 one CTA, 3 one cluster).
+int sweep_form_setting();
 lsq_status sparse_solve(const lsq_matrix* A, const lsq_precond* P, const double* B, const double* Hcols,
                         int64_t k, int64_t ldb, double* X, int64_t ldx, const lsq_opts* o, lsq_info* info,
                         cudaStream_t st);

@@ -354,3 +354,79 @@ def test_graph_laplacian_singular_matches_oracle(lsq, orc, n_param, sweeps, tol,
                 return v - (np.bincount(lab, v) / np.bincount(lab))[lab]
             assert_solution(B @ X[c], B @ x_or, kappa_eff, f"fitted values column {c}")
             assert_solution(rng_part(X[c]), rng_part(x_or), kappa_eff, f"range part column {c}")
+
+
+@pytest.fixture
+def sweep_form(lsq):
+    """Sets the process-wide form of the one-column sweeps for one test, then restores it."""
+    def set_form(f):
+        lsq.set_sweep_form(f)
+    yield set_form
+    lsq.set_sweep_form(0)
+
+
+@pytest.mark.parametrize("sweeps", [1, 2])
+@pytest.mark.parametrize("case", ["sprand", "graph", "wide", "mid", "graph_wide"])
+def test_sweep_forms_are_bit_identical(lsq, orc, sweep_form, case, sweeps):
+    """The grid, one-CTA and one-cluster forms of a sweep visit the same rows in the same level
+    order with the same per-row arithmetic (a lane's entries in order, then the warp sum), so
+    they give the same bits; each against the literal Alg. 3 at 1e-11."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003, sweeps=sweeps)
+    R = np.random.default_rng(5 + sweeps).standard_normal((3, seen["n"]))
+    Rt = torch.from_numpy(R).cuda()
+    outs = {}
+    for form in (1, 2, 3):
+        sweep_form(form)
+        outs[form] = P.apply(Rt).cpu().numpy()
+    for c in range(3):
+        ref = orc.sgs_apply(Mo, R[c], sweeps)
+        for form in (1, 2, 3):
+            assert rel(outs[form][c], ref) <= 1e-11, (form, c)
+    assert np.array_equal(outs[1], outs[2]), "grid and one-CTA sweeps differ"
+    assert np.array_equal(outs[1], outs[3]), "grid and cluster sweeps differ"
+
+
+@pytest.mark.parametrize("case", ["sprand", "mid", "graph"])
+def test_cluster_sweep_solve_matches_oracle(lsq, orc, sweep_form, case):
+    """A whole one-column solve with the cluster-form sweeps (the first carrying the
+    convergence check) against the oracle, and bit for bit against the grid form."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 2029)
+    xs, b = W.rhs_for(seen, 1, 1e-3, 23)
+    B = torch.from_numpy(b[0]).cuda()
+    sweep_form(3)
+    X3, i3 = lsq.lsq_pcg_solve(Mx, P, B, o)
+    sweep_form(1)
+    X1, i1 = lsq.lsq_pcg_solve(Mx, P, B, o)
+    assert np.array_equal(X3.cpu().numpy(), X1.cpu().numpy()) and int(i3.iters[0]) == int(i1.iters[0])
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer)
+    assert i3.converged[0] == 1 and oi["converged"] == 1 and i3.relres_true[0] <= o.tol
+    x = X3.cpu().numpy().reshape(-1)
+    kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
+    assert_solution(x, y / smp.d, kappa, f"{case} cluster sweeps")
+    assert_iterations(i3.iters[0], oi["iters"], _variants(orc, seen, smp, Mo, b[0], o), f"{case} cluster sweeps")
+
+
+@pytest.mark.parametrize("case,k,sweeps", [("sprand", 3, 1), ("sprand", 5, 2), ("graph", 4, 1), ("mid", 4, 2),
+                                           ("wide", 2, 1), ("wide", 17, 1)])
+def test_block_cluster_sweep_matches_oracle(lsq, orc, sweep_form, case, k, sweeps):
+    """The block solve with its sweeps in one thread-block cluster (form 3) against the oracle;
+    where the shape picks the CTA-per-row form anyway (more than 96 dependency entries per row),
+    bit for bit against it, since both sum a row's entries in the same order."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 717, sweeps=sweeps)
+    xs, b = W.rhs_for(seen, k, 1e-3, 718)
+    B = torch.from_numpy(b).cuda()
+    sweep_form(3)
+    X3, i3 = lsq.lsq_pcg_solve(Mx, P, B, o)
+    sweep_form(1)
+    X1, i1 = lsq.lsq_pcg_solve(Mx, P, B, o)
+    X3 = X3.cpu().numpy()
+    dep = (int(i3.nnz_M) - seen["n"]) / (2.0 * seen["n"])
+    if dep > 96.0:
+        assert np.array_equal(X3, X1.cpu().numpy()) and list(i3.iters) == list(i1.iters)
+    kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
+    for c in sorted({0, k // 2, k - 1}):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=sweeps)
+        assert i3.converged[c] == 1 and oi["converged"] == 1 and i3.relres_true[c] <= o.tol
+        assert_solution(X3[c], y / smp.d, kappa, f"cluster block {case} column {c}")
+        assert_iterations(i3.iters[c], oi["iters"], _variants(orc, seen, smp, Mo, b[c], o),
+                          f"cluster block {case} t={sweeps} column {c}")

@@ -635,9 +635,38 @@ def sparse_config(which, tol=1e-10, maxit=1000000, sweeps=1, inner_tol=0.0, step
                         "bytes_per_iter": per_iter,
                         "note": "algorithmic bytes per iteration (A once, M once, ~10 n x k vector "
                                 "passes) x iterations / solve time"}}
+    if sweeps > 0:
+        out["sweep"] = sweep_latency_bound(api, P, mat["n"], sweeps, int(info.levels))
     if cpu:
         out["cpu_baseline"] = oracle_csr_sample(mat, b[0], 1003, it, k)
     return out
+
+
+def sweep_latency_bound(api, P, n, sweeps, levels, reps=3):
+    """The one-column Gauss-Seidel sweep (Alg. 3) against its latency bound: a sweep is a chain
+    of `levels` levels, each needing at least one hand-off of a value between SMs (half the
+    measured round trip) and one dependent load of it (an L2 load).  The sweep time is the
+    preconditioner application (t forward + t backward sweeps) over 2t, CUDA events."""
+    import torch
+    lat = api.measure_latency()
+    R = torch.randn(n, dtype=torch.float64, device="cuda")
+    P.apply(R)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        P.apply(R)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps / (2 * sweeps)
+    per_level_ns = 0.5 * lat["sm_round_trip_ns"] + lat["l2_load_ns"]
+    bound = levels * per_level_ns / 1e6
+    return {"ms_per_sweep": ms, "levels": levels, "us_per_level": 1e3 * ms / max(levels, 1),
+            "latency_ns": lat, "bound": "latency", "bound_ms_per_sweep": bound,
+            "frac": bound / ms if ms > 0 else None,
+            "note": "bound = levels x (half an SM-to-SM round trip + one dependent L2 load), measured "
+                    "on this device by lsq_measure_latency; sweep = one-column preconditioner "
+                    "application / 2t"}
 
 
 def run_sparse_workload(args):

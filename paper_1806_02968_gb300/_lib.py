@@ -67,6 +67,7 @@ PROTOTYPES = {
     "lsq_kernel_launch_count": (I64, []),
     "lsq_set_wait_limit": (C.c_int, [I64]),
     "lsq_set_sweep_form": (C.c_int, [C.c_int32]),
+    "lsq_measure_latency": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lsq_shard_colmax": (C.c_int, [P, P, P]),
     "lsq_shard_colsum": (C.c_int, [P, P, P, P]),
     "lsq_shard_weights": (C.c_int, [P, P, P, P, P, P, P, P]),

@@ -53,6 +53,7 @@ struct SpArgs {
     const int64_t* loff_b;
     int64_t one_f, one_b;       // level count when that direction runs in one CTA, else 0
     int64_t cl_f, cl_b;         // level count when that direction runs in one cluster, else 0
+    int64_t nlev_f, nlev_b;     // level counts of the two schedules
     int cl_lg;                  // log2 of that cluster's size
     int lpr, lpc;               // lanes per row of A, lanes per column of A (powers of two <= 32)
     int sweeps;
@@ -702,7 +703,8 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
     (void)idx;
     SpArgs av = a;
     void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &check, &nparts};
-    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(SP_T), params, 0, st));
+    const int g_sweep = sweep_grid(grid, a.n, FWD ? a.nlev_f : a.nlev_b, SP_T / 32);
+    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(g_sweep), dim3(SP_T), params, 0, st));
     count_launch();
     return LSQ_OK;
 }
@@ -773,7 +775,8 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.w = vec + 5 * n; a.e0 = vec + 6 * n; a.e1 = vec + 7 * n; a.h = vec + 8 * n;
     double* tmpv = vec + 9 * n;
     a.q = (double*)(base + o_q);
-    a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n);
+    a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; a.nlev_f = SH->nlev_f; a.nlev_b = SH->nlev_b;
+    choose_sweep_form(a, SH, n);
     auto lanes_for = [](double mean) { int L = 1; while (L < 32 && L < mean) L <<= 1; return L; };
     a.lpr = lanes_for((double)nnz / (double)m);
     a.lpc = lanes_for((double)nnz / (double)n);
@@ -982,7 +985,8 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
     a.mval = P->op_dtype == LSQ_F32 ? (const void*)SH->mval32 : (const void*)SH->mval;
     a.dinv = SH->dinv; a.sched_f = SH->sched_f; a.sched_b = SH->sched_b; a.sweeps = P->sweeps;
     a.e0 = (double*)(base + o_e); a.e1 = a.e0 + n;
-    a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; choose_sweep_form(a, SH, n);
+    a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; a.nlev_f = SH->nlev_f; a.nlev_b = SH->nlev_b;
+    choose_sweep_form(a, SH, n);
     a.S = (SpState*)(base + o_S);
     if (P->sweeps == 0) {
         LSQ_CUDA(cudaMemcpyAsync(e, r, 8 * (size_t)n * k, cudaMemcpyDeviceToDevice, st));

@@ -241,7 +241,8 @@ static unsigned bk_grid(int64_t work, int64_t cap) {
 // Cooperative launch: every warp of the sweep must be resident for the level waits to end.
 // The grid (SMs x resident blocks) is computed once per kernel.
 static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const double* r, const double* eold,
-                                  double* enew, int identity, int idx, cudaStream_t st) {
+                                  double* enew, int identity, int idx, int64_t nlev, int units_per_block,
+                                  cudaStream_t st) {
     static std::mutex mu;
     static std::unordered_map<const void*, int> grids;
     int grid = 0;
@@ -265,7 +266,8 @@ static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const doubl
     count_launch();
     BkArgs av = a;
     void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &idx};
-    LSQ_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BK_T), params, 0, st));
+    const int g_sweep = sweep_grid(grid, a.n, nlev, units_per_block);
+    LSQ_CUDA(cudaLaunchCooperativeKernel(kern, dim3(g_sweep), dim3(BK_T), params, 0, st));
     count_launch();
     return LSQ_OK;
 }
@@ -461,7 +463,8 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         lsq_status q;
         if (fwd && cl_f) q = bk_launch_sweep_cl(cf, a, r, eold, enew, identity, SH->loff_f, SH->nlev_f, st);
         else if (!fwd && cl_b) q = bk_launch_sweep_cl(cb, a, r, eold, enew, identity, SH->loff_b, SH->nlev_b, st);
-        else q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, st);
+        else q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, fwd ? SH->nlev_f : SH->nlev_b,
+                                 smode == 2 ? 1 : BK_T / 32, st);
         if (q != LSQ_OK) sweep_status = q;
     };
     // z = P g: t forward then t backward sweeps

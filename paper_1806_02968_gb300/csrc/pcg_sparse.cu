@@ -94,8 +94,9 @@ constexpr int SP_T = 256;
 enum { SPM_MATVEC = 0, SPM_RHS = 1, SPM_RESID = 2 };
 
 // q_i = sum_e a_e x_{col e} (x = D^{-1} p or D^{-1} y), or b_i, or b_i - that.  A group of
-// LPR lanes (a power of two, about the mean row length) takes 4 consecutive rows per step, so
-// that the loads of 4 rows are in flight together; each row sums its entries in a fixed order.
+// LPR lanes (a power of two, about the mean row length) takes 4 consecutive rows per step and
+// walks their entries flat, so that the loads of 4 rows are in flight together; each row sums
+// its entries in a fixed order.
 template <int DT>
 __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_res, const double* x) {
     __shared__ double sh[40];
@@ -114,10 +115,34 @@ __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_re
         for (int r = 0; r < 5; ++r) rp[r] = a.row_ptr[min(i0 + r, a.m)];
         double dot[4] = {0.0, 0.0, 0.0, 0.0};
         if (mode != SPM_RHS) {
+            // the 4 rows' entries are contiguous: walk them flat, 4 per lane at a time, all
+            // loads (and then all gathers) of a step in flight together; each entry goes to
+            // its row's sum, every row still summing its entries in order per lane
+            for (int64_t e0 = rp[0] + sub; e0 < rp[4]; e0 += 4 * L) {
+                double av[4];
+                int32_t cv[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                for (int64_t e = rp[r] + sub; e < rp[r + 1]; e += L)
-                    dot[r] = fma(Val<DT>::load(vals, e), x[a.col_idx[e]], dot[r]);
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t e = e0 + (int64_t)u * L;
+                    const bool in = e < rp[4];
+                    av[u] = in ? (double)Val<DT>::load(vals, e) : 0.0;
+                    cv[u] = in ? a.col_idx[e] : -1;
+                }
+                double xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = cv[u] >= 0 ? x[cv[u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t e = e0 + (int64_t)u * L;
+                    if (cv[u] >= 0) {
+                        const int r = (e >= rp[1]) + (e >= rp[2]) + (e >= rp[3]);
+                        if (r == 0) dot[0] = fma(av[u], xv[u], dot[0]);
+                        else if (r == 1) dot[1] = fma(av[u], xv[u], dot[1]);
+                        else if (r == 2) dot[2] = fma(av[u], xv[u], dot[2]);
+                        else dot[3] = fma(av[u], xv[u], dot[3]);
+                    }
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r)

@@ -411,13 +411,15 @@ LSQ_API lsq_status lsq_set_wait_limit(int64_t max_polls);
 LSQ_API lsq_status lsq_set_sweep_form(int32_t form);
 
 /* Latency figures of the current device, for the latency bound of the level-ordered sweeps of
- * Alg. 3 (a diagnostic, not in the paper).  out_ns (host, 4 doubles, caller-owned) receives,
+ * Alg. 3 (a diagnostic, not in the paper).  out_ns (host, 5 doubles, caller-owned) receives,
  * in nanoseconds:
  *   [0] one dependent load from L2 (one thread chasing a scattered cycle through 64 MB),
  *   [1] the round trip of a value between two SMs through global memory (two CTAs of one
- *       cooperative launch hand a counter back and forth),
+ *       cooperative launch hand a counter back and forth with volatile loads and stores, the
+ *       value being the flag, as in the sweeps),
  *   [2] one barrier of an 8-CTA thread-block cluster,
- *   [3] one dependent load from another CTA's shared memory in a 2-CTA cluster.
+ *   [3] one dependent load from another CTA's shared memory in a 2-CTA cluster,
+ *   [4] the round trip of [1] with a fence before each store.
  * Allocates and frees its own 64 MB buffer and synchronises the stream.  LSQ_ERR_TIMEOUT if the
  * hand-off ran out of polls, LSQ_ERR_CUDA if a probe could not be launched. */
 LSQ_API lsq_status lsq_measure_latency(double* out_ns, void* stream);

@@ -341,12 +341,12 @@ def set_sweep_form(form: int = 0):
 
 def measure_latency(stream=None) -> dict:
     """The device's latency figures in ns (lsq_measure_latency): a dependent L2 load, a value's
-    round trip between two SMs through global memory, an 8-CTA cluster barrier and a
-    dependent load from another CTA's shared memory."""
-    out = (C.c_double * 4)()
+    round trip between two SMs through global memory (without and with a fence before each
+    store), an 8-CTA cluster barrier and a dependent load from another CTA's shared memory."""
+    out = (C.c_double * 5)()
     _check(L.load().lsq_measure_latency(C.cast(out, C.c_void_p), _stream(stream)), "lsq_measure_latency")
     return {"l2_load_ns": out[0], "sm_round_trip_ns": out[1], "cluster_barrier_ns": out[2],
-            "dsmem_load_ns": out[3]}
+            "dsmem_load_ns": out[3], "sm_round_trip_fenced_ns": out[4]}
 
 
 def solve(A: Matrix, b, o=None, stream=None):

@@ -4,7 +4,8 @@
 //   k_lat_chase   one thread follows a pseudo-random cycle through a 64 MB buffer (L2): the
 //                 time of one dependent load;
 //   k_lat_flag    two CTAs (one cooperative launch, so both are resident) hand a counter back
-//                 and forth through global memory: the round trip of a value between two SMs;
+//                 and forth through global memory: the round trip of a value between two SMs,
+//                 without and with a fence before each store;
 //   k_lat_clbar   8 CTAs of one cluster pass cluster barriers: the time of one barrier;
 //   k_lat_dsmem   one thread of CTA 0 follows a cycle through CTA 1's shared memory: the time
 //                 of one dependent load from another CTA of the cluster.
@@ -45,8 +46,10 @@ __global__ void k_lat_chase(const unsigned* buf, int hops, unsigned* sink, unsig
     ns[0] = t1 - t0;
 }
 
-// CTA 0 waits for even values and writes the next odd one, CTA 1 the reverse
-__global__ void k_lat_flag(unsigned* flag, int rounds, unsigned* err, unsigned long long* ns) {
+// CTA 0 waits for even values and writes the next odd one, CTA 1 the reverse.  fenced = 0:
+// plain volatile loads and stores, the value being the flag, as in the sweeps' hand-offs;
+// fenced = 1: a fence before each store, as a hand-off that publishes other data needs.
+__global__ void k_lat_flag(unsigned* flag, int rounds, int fenced, unsigned* err, unsigned long long* ns) {
     if (threadIdx.x != 0) return;
     volatile unsigned* f = flag;
     const unsigned long long t0 = lat_now();
@@ -56,11 +59,11 @@ __global__ void k_lat_flag(unsigned* flag, int rounds, unsigned* err, unsigned l
         while (*f != want) {
             if (++polls > (1u << 24)) { atomicOr(err, 1u); return; }
         }
-        __threadfence();
+        if (fenced) __threadfence();
         *f = want + 1u;
     }
     const unsigned long long t1 = lat_now();
-    if (blockIdx.x == 0) ns[1] = t1 - t0;
+    if (blockIdx.x == 0) ns[fenced ? 4 : 1] = t1 - t0;
 }
 
 __global__ void k_lat_clbar(int rounds, unsigned long long* ns) {
@@ -120,18 +123,18 @@ extern "C" lsq_status lsq_measure_latency(double* out_ns, void* stream) {
     unsigned* buf = nullptr;
     unsigned long long* dev = nullptr;
     LSQ_CUDA(cudaMalloc(&buf, (size_t)LAT_LINES * LAT_LINE_WORDS * sizeof(unsigned)));
-    const size_t small = 4 * sizeof(unsigned long long) + 4 * sizeof(unsigned) + 64;
+    const size_t small = 5 * sizeof(unsigned long long) + 4 * sizeof(unsigned) + 64;
     if (cudaMalloc(&dev, small) != cudaSuccess) {
         cudaFree(buf);
         set_error("lsq_measure_latency: cudaMalloc failed");
         return LSQ_ERR_NOMEM;
     }
     unsigned long long* ns = dev;
-    unsigned* flag = reinterpret_cast<unsigned*>(dev + 4);
+    unsigned* flag = reinterpret_cast<unsigned*>(dev + 5);
     unsigned* err = flag + 1;
     unsigned* sink = flag + 2;
     lsq_status status = LSQ_OK;
-    unsigned long long h_ns[4] = {0, 0, 0, 0};
+    unsigned long long h_ns[5] = {0, 0, 0, 0, 0};
     unsigned h_err = 0;
     auto step = [&](cudaError_t e, const char* what) {
         if (e != cudaSuccess && status == LSQ_OK) {
@@ -145,9 +148,10 @@ extern "C" lsq_status lsq_measure_latency(double* out_ns, void* stream) {
     k_lat_chase<<<1, 1, 0, st>>>(buf, LAT_HOPS, sink, ns);
     count_launch(3);
     step(cudaGetLastError(), "chase");
-    {
+    for (int fenced = 0; fenced < 2; ++fenced) {
         int rounds = LAT_ROUNDS;
-        void* params[] = {&flag, &rounds, &err, &ns};
+        step(cudaMemsetAsync(flag, 0, sizeof(unsigned), st), "memset");
+        void* params[] = {&flag, &rounds, &fenced, &err, &ns};
         step(cudaLaunchCooperativeKernel((const void*)k_lat_flag, dim3(2), dim3(32), params, 0, st), "flag");
         count_launch();
     }
@@ -168,5 +172,6 @@ extern "C" lsq_status lsq_measure_latency(double* out_ns, void* stream) {
     out_ns[1] = (double)h_ns[1] / LAT_ROUNDS;
     out_ns[2] = (double)h_ns[2] / LAT_ROUNDS;
     out_ns[3] = (double)h_ns[3] / LAT_HOPS;
+    out_ns[4] = (double)h_ns[4] / LAT_ROUNDS;
     return LSQ_OK;
 }

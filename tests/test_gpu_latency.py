@@ -13,5 +13,6 @@ def test_latency_probe_values_are_plausible(lsq):
     assert 20.0 < lat["dsmem_load_ns"] < 5000.0, lat
     assert 20.0 < lat["cluster_barrier_ns"] < 20000.0, lat
     assert 50.0 < lat["sm_round_trip_ns"] < 50000.0, lat
+    assert 50.0 < lat["sm_round_trip_fenced_ns"] < 50000.0, lat
     # a value handed between SMs through memory costs at least one L2 access each way
     assert lat["sm_round_trip_ns"] > lat["l2_load_ns"]

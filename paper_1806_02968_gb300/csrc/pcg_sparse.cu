@@ -15,6 +15,7 @@
 // converged.
 #include "sparse.cuh"
 #include "values.cuh"
+#include "dfloat.cuh"
 
 #include <cooperative_groups.h>
 
@@ -211,12 +212,81 @@ __global__ void __launch_bounds__(SP_T) k_sp_update(SpArgs a, int nparts) {
 // t = 1): r - L e_old = D e_old, so e_new_j = e_old_j - (sum_{k>j} M_jk e_new_k) / M_jj.
 constexpr int SW_PF = 16;           // dependency entries per lane held in registers
 
+// The row arithmetic of a sweep.  A sweep is a chain of dependent row sums, one per level, so
+// the latency of each operation counts, not its throughput.  With FP64 M the sums are FP64
+// (SwArith<double>).  With FP32 M they are double-float on the FP32 units (SwArith<float>,
+// about 48 significant bits): on GB300 a dependent FP64 operation takes ~64 cycles and an
+// FP64 shuffle-and-add ~108, against 4.5 and 32 for FP32.  Sweep vectors hold one 8-byte slot
+// per row: an FP64 value, or a (hi, lo) float pair; only the sweep's own buffers hold pairs,
+// and `out64` receives FP64 values where a caller needs them.
+template <typename MT> struct SwArith;
+template <> struct SwArith<double> {
+    typedef double Acc;
+    typedef double Val;
+    static __device__ __forceinline__ Acc zero() { return 0.0; }
+    static __device__ __forceinline__ Val from_bits(unsigned long long u) { return __longlong_as_double((long long)u); }
+    static __device__ __forceinline__ unsigned long long to_bits(Val v) { return (unsigned long long)__double_as_longlong(v); }
+    static __device__ __forceinline__ Val load(const double* p, int64_t k) { return p[k]; }
+    static __device__ __forceinline__ void mad(Acc& acc, double m, Val v) { acc = fma(m, v, acc); }
+    static __device__ __forceinline__ Acc total(Acc a) { return warp_sum(a); }
+    static __device__ __forceinline__ Val from_double(double x) { return x; }
+    static __device__ __forceinline__ double to_double(Val v) { return v; }
+    static __device__ __forceinline__ Val finish(Val base, Acc acc, Val dj, bool identity) {
+        return identity ? base - acc * dj : (base - acc) * dj;
+    }
+};
+template <> struct SwArith<float> {
+    typedef f2 Acc;
+    typedef f2 Val;
+    static __device__ __forceinline__ Acc zero() { return f2{0.f, 0.f}; }
+    static __device__ __forceinline__ Val from_bits(unsigned long long u) {
+        return f2{__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32))};
+    }
+    static __device__ __forceinline__ unsigned long long to_bits(Val v) {
+        return (unsigned long long)__float_as_uint(v.hi) | ((unsigned long long)__float_as_uint(v.lo) << 32);
+    }
+    static __device__ __forceinline__ Val load(const double* p, int64_t k) {
+        return from_bits(reinterpret_cast<const unsigned long long*>(p)[k]);
+    }
+    // acc += m v in the cascaded form (the high word takes the rounded sum, the errors of the
+    // sum and of the product gather in the low word; total() renormalises)
+    static __device__ __forceinline__ void mad(Acc& acc, float m, Val v) {
+        float p, pe;
+        two_prod(m, v.hi, p, pe);
+        pe = fmaf(m, v.lo, pe);
+        float s, e;
+        two_sum(acc.hi, p, s, e);
+        acc.hi = s;
+        acc.lo += e + pe;
+    }
+    static __device__ __forceinline__ Acc total(Acc a) { return df_warp_sum(df_norm(a)); }
+    static __device__ __forceinline__ Val from_double(double x) { return df_from_double(x); }
+    static __device__ __forceinline__ double to_double(Val v) { return df_to_double(v); }
+    static __device__ __forceinline__ f2 mul(f2 a, f2 b) {
+        float p, e;
+        two_prod(a.hi, b.hi, p, e);
+        e = fmaf(a.hi, b.lo, e);
+        e = fmaf(a.lo, b.hi, e);
+        const float hi = p + e;
+        return f2{hi, e - (hi - p)};
+    }
+    static __device__ __forceinline__ f2 sub(f2 a, f2 b) {
+        f2 r = a;
+        df_add(r, f2{-b.hi, -b.lo});
+        return r;
+    }
+    static __device__ __forceinline__ Val finish(Val base, Acc acc, Val dj, bool identity) {
+        return identity ? sub(base, mul(acc, dj)) : mul(sub(base, acc), dj);
+    }
+};
+
 // The grid sweep with the values themselves as completion flags.  Before the sweep every slot
-// of e_new holds SWEEP_EMPTY, a signalling NaN that no arithmetic produces; a row polls the
-// values it depends on (volatile loads, bounded) until none is SWEEP_EMPTY, then writes its own
-// value.  A row thus waits for its own dependencies only, and no counter has to be published
-// and read back between levels.  Warp w takes schedule slots w, w + W, ... (rows sorted by
-// level), all warps resident, so every wait ends.
+// of e_new holds SWEEP_EMPTY, a pattern no arithmetic produces (an FP64 signalling NaN, or a
+// float pair whose low word is a NaN of a form no operation returns); a row polls the values
+// it depends on (volatile loads, bounded) until none is SWEEP_EMPTY, then writes its own value.
+// A row thus waits for its own dependencies only, and no counter has to be published and read
+// back between levels.  Warp w takes schedule slots w, w + W, ... (rows sorted by level), all
+// warps resident, so every wait ends.
 constexpr unsigned long long SWEEP_EMPTY = 0xFFF7DEADBEEFCAFEull;
 constexpr int SWG = 8;                 // dependency values a lane loads before it polls
 constexpr unsigned SW_SPIN = 4;        // polls before the first back-off
@@ -231,9 +301,16 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const double* p) {
     asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void st_volatile_u64(double* p, unsigned long long v) {
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r, const double* e_old,
-                                                      double* e_new, int identity, int check, int nparts) {
+                                                      double* e_new, double* out64, int identity, int check,
+                                                      int nparts) {
+    typedef SwArith<MT> A;
+    typedef typename A::Acc Acc;
+    typedef typename A::Val Val;
     __shared__ double sh[40];
     __shared__ int s_stop;
     if (a.S->done) return;
@@ -261,7 +338,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
     const bool other = !identity && e_old != nullptr;
     bool ok = true;
     // the values of up to SWG dependencies per lane: issue all loads, then poll the missing
-    auto gather = [&](const int32_t (&kk)[SWG], const double (&mm)[SWG], double& acc) {
+    auto gather = [&](const int32_t (&kk)[SWG], const MT (&mm)[SWG], Acc& acc) {
         unsigned long long u[SWG];
 #pragma unroll
         for (int c = 0; c < SWG; ++c) u[c] = kk[c] >= 0 ? ld_volatile_u64(e_new + kk[c]) : 0ull;
@@ -286,34 +363,35 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
         }
 #pragma unroll
         for (int c = 0; c < SWG; ++c)
-            if (kk[c] >= 0) acc = fma(mm[c], __longlong_as_double((long long)u[c]), acc);
+            if (kk[c] >= 0) A::mad(acc, mm[c], A::from_bits(u[c]));
     };
     for (int64_t slot = gw; slot < a.n; slot += W) {
         const int64_t j = sched[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
         const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
-        double acc = 0.0;
+        Acc acc = A::zero();
         if (other)
-            for (int64_t e = o0 + lane; e < o1; e += 32) acc = fma((double)mv[e], e_old[a.mcol[e]], acc);
-        const double base = identity ? e_old[j] : r[j];
-        const double dj = a.dinv[j];
+            for (int64_t e = o0 + lane; e < o1; e += 32) A::mad(acc, mv[e], A::load(e_old, a.mcol[e]));
+        const Val base = identity ? A::load(e_old, j) : A::from_double(r[j]);
+        const Val dj = A::from_double(a.dinv[j]);
         for (int64_t b0 = d0 + lane; b0 < d1; b0 += 32 * SWG) {
             int32_t kk[SWG];
-            double mm[SWG];
+            MT mm[SWG];
 #pragma unroll
             for (int c = 0; c < SWG; ++c) {
                 const int64_t e = b0 + 32 * c;
                 kk[c] = -1;
-                mm[c] = 0.0;
-                if (e < d1) { kk[c] = a.mcol[e]; mm[c] = (double)mv[e]; }
+                mm[c] = MT(0);
+                if (e < d1) { kk[c] = a.mcol[e]; mm[c] = mv[e]; }
             }
             gather(kk, mm, acc);
         }
-        acc = warp_sum(acc);
+        acc = A::total(acc);
         if (lane == 0) {
-            const double v = identity ? base - acc * dj : (base - acc) * dj;
-            asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(e_new + j), "d"(v) : "memory");
+            const Val v = A::finish(base, acc, dj, identity != 0);
+            st_volatile_u64(e_new + j, A::to_bits(v));
+            if (out64) out64[j] = A::to_double(v);
         }
         __syncwarp();
     }
@@ -328,8 +406,11 @@ __global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r,
 constexpr int S1_T = 512;
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(S1_T, 1) k_sp_sweep_1cta(SpArgs a, const double* r, const double* e_old,
-                                                           double* e_new, int identity, int check, int nparts,
-                                                           int64_t nlev) {
+                                                           double* e_new, double* out64, int identity, int check,
+                                                           int nparts, int64_t nlev) {
+    typedef SwArith<MT> A;
+    typedef typename A::Acc Acc;
+    typedef typename A::Val Val;
     __shared__ double sh[40];
     __shared__ int s_stop;
     if (a.S->done) return;
@@ -356,10 +437,11 @@ __global__ void __launch_bounds__(S1_T, 1) k_sp_sweep_1cta(SpArgs a, const doubl
     // one row's inputs that do not depend on this sweep
     struct Row {
         int64_t j, d0, d1;
-        double base;        // r_j (or e_old_j for the identity form)
-        double acc;         // this lane's other-side terms
+        Val base;           // r_j (or e_old_j for the identity form)
+        Val dj;             // 1 / M_jj
+        Acc acc;            // this lane's other-side terms
         int32_t kk[SW_PF];
-        double mm[SW_PF];
+        MT mm[SW_PF];
     };
     auto load_row = [&](int64_t j, Row& R) {
         R.j = j;
@@ -367,41 +449,43 @@ __global__ void __launch_bounds__(S1_T, 1) k_sp_sweep_1cta(SpArgs a, const doubl
         R.d0 = FWD ? e0 : ed + 1;
         R.d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
-        R.base = identity ? e_old[j] : r[j];
-        R.acc = 0.0;
+        R.base = identity ? A::load(e_old, j) : A::from_double(r[j]);
+        R.dj = A::from_double(a.dinv[j]);
+        R.acc = A::zero();
         if (other)
-            for (int64_t e = o0 + lane; e < o1; e += 32) R.acc = fma((double)mv[e], e_old[a.mcol[e]], R.acc);
+            for (int64_t e = o0 + lane; e < o1; e += 32) A::mad(R.acc, mv[e], A::load(e_old, a.mcol[e]));
 #pragma unroll
         for (int c = 0; c < SW_PF; ++c) {
             const int64_t e = R.d0 + lane + 32 * c;
             R.kk[c] = -1;
-            R.mm[c] = 0.0;
-            if (e < R.d1) { R.kk[c] = a.mcol[e]; R.mm[c] = (double)mv[e]; }
+            R.mm[c] = MT(0);
+            if (e < R.d1) { R.kk[c] = a.mcol[e]; R.mm[c] = mv[e]; }
         }
     };
     auto finish_row = [&](const Row& R) {
-        double acc = R.acc;
+        Acc acc = R.acc;
 #pragma unroll
         for (int c = 0; c < SW_PF; ++c)
-            if (R.kk[c] >= 0) acc = fma(R.mm[c], e_new[R.kk[c]], acc);
+            if (R.kk[c] >= 0) A::mad(acc, R.mm[c], A::load(e_new, R.kk[c]));
         for (int64_t base = R.d0 + 32 * SW_PF; base < R.d1; base += 32 * 8) {
             int32_t k2[8];
-            double m2[8];
+            MT m2[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t e = base + lane + 32 * u;
                 k2[u] = -1;
-                m2[u] = 0.0;
-                if (e < R.d1) { k2[u] = a.mcol[e]; m2[u] = (double)mv[e]; }
+                m2[u] = MT(0);
+                if (e < R.d1) { k2[u] = a.mcol[e]; m2[u] = mv[e]; }
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (k2[u] >= 0) acc = fma(m2[u], e_new[k2[u]], acc);
+                if (k2[u] >= 0) A::mad(acc, m2[u], A::load(e_new, k2[u]));
         }
-        acc = warp_sum(acc);
+        acc = A::total(acc);
         if (lane == 0) {
-            const double dj = a.dinv[R.j];
-            e_new[R.j] = identity ? R.base - acc * dj : (R.base - acc) * dj;
+            const Val v = A::finish(R.base, acc, R.dj, identity != 0);
+            reinterpret_cast<unsigned long long*>(e_new)[R.j] = A::to_bits(v);
+            if (out64) out64[R.j] = A::to_double(v);
         }
     };
     Row cur;
@@ -434,10 +518,13 @@ __global__ void __launch_bounds__(S1_T, 1) k_sp_sweep_1cta(SpArgs a, const doubl
 constexpr int SC_T = 512;
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(SC_T, 1) k_sp_sweep_cl(SpArgs a, const double* r, const double* e_old,
-                                                         double* e_new, int identity, int check, int nparts,
-                                                         int64_t nlev, int lg) {
+                                                         double* e_new, double* out64, int identity, int check,
+                                                         int nparts, int64_t nlev, int lg) {
     namespace cg = cooperative_groups;
-    extern __shared__ __align__(16) double xs[];   // this CTA's slots of e_new
+    typedef SwArith<MT> A;
+    typedef typename A::Acc Acc;
+    typedef typename A::Val Val;
+    extern __shared__ __align__(16) unsigned long long xs[];   // this CTA's slots of e_new
     __shared__ double sh[40];
     __shared__ int s_stop;
     // Every CTA takes the same exits before the first cluster barrier: done is only written
@@ -471,7 +558,8 @@ __global__ void __launch_bounds__(SC_T, 1) k_sp_sweep_cl(SpArgs a, const double*
     const bool other = !identity && e_old != nullptr;
     struct Row {
         int64_t j, d0, d1;
-        double base, acc;
+        Val base, dj;
+        Acc acc;
         int32_t kk[SW_PF];
         MT mm[SW_PF];
     };
@@ -481,10 +569,11 @@ __global__ void __launch_bounds__(SC_T, 1) k_sp_sweep_cl(SpArgs a, const double*
         R.d0 = FWD ? e0 : ed + 1;
         R.d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
-        R.base = identity ? e_old[j] : r[j];
-        R.acc = 0.0;
+        R.base = identity ? A::load(e_old, j) : A::from_double(r[j]);
+        R.dj = A::from_double(a.dinv[j]);
+        R.acc = A::zero();
         if (other)
-            for (int64_t e = o0 + lane; e < o1; e += 32) R.acc = fma((double)mv[e], e_old[a.mcol[e]], R.acc);
+            for (int64_t e = o0 + lane; e < o1; e += 32) A::mad(R.acc, mv[e], A::load(e_old, a.mcol[e]));
 #pragma unroll
         for (int c = 0; c < SW_PF; ++c) {
             const int64_t e = R.d0 + lane + 32 * c;
@@ -493,38 +582,40 @@ __global__ void __launch_bounds__(SC_T, 1) k_sp_sweep_cl(SpArgs a, const double*
             if (e < R.d1) { R.kk[c] = a.mcol[e]; R.mm[c] = mv[e]; }
         }
     };
-    auto gather = [&](int32_t k) -> double {
-        const double* src = cl.map_shared_rank(xs, (unsigned)k & cmask);
-        return src[(unsigned)k >> lg];
+    auto gather = [&](int32_t k) -> Val {
+        const unsigned long long* src = cl.map_shared_rank(xs, (unsigned)k & cmask);
+        return A::from_bits(src[(unsigned)k >> lg]);
     };
     auto finish_row = [&](const Row& R) {
-        double v[SW_PF];
+        Val v[SW_PF];
 #pragma unroll
-        for (int c = 0; c < SW_PF; ++c) v[c] = R.kk[c] >= 0 ? gather(R.kk[c]) : 0.0;
-        double acc = R.acc;
+        for (int c = 0; c < SW_PF; ++c) v[c] = R.kk[c] >= 0 ? gather(R.kk[c]) : A::from_bits(0ull);
+        Acc acc = R.acc;
 #pragma unroll
-        for (int c = 0; c < SW_PF; ++c) acc = fma((double)R.mm[c], v[c], acc);
+        for (int c = 0; c < SW_PF; ++c)
+            if (R.kk[c] >= 0) A::mad(acc, R.mm[c], v[c]);
         for (int64_t b0 = R.d0 + 32 * SW_PF; b0 < R.d1; b0 += 32 * 8) {
             int32_t k2[8];
-            double m2[8];
+            MT m2[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t e = b0 + lane + 32 * u;
                 k2[u] = -1;
-                m2[u] = 0.0;
-                if (e < R.d1) { k2[u] = a.mcol[e]; m2[u] = (double)mv[e]; }
+                m2[u] = MT(0);
+                if (e < R.d1) { k2[u] = a.mcol[e]; m2[u] = mv[e]; }
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (k2[u] >= 0) acc = fma(m2[u], gather(k2[u]), acc);
+                if (k2[u] >= 0) A::mad(acc, m2[u], gather(k2[u]));
         }
-        acc = warp_sum(acc);
+        acc = A::total(acc);
         if (lane == 0) {
-            const double dj = a.dinv[R.j];
-            const double val = identity ? R.base - acc * dj : (R.base - acc) * dj;
-            double* dst = cl.map_shared_rank(xs, (unsigned)R.j & cmask);
-            dst[(unsigned)R.j >> lg] = val;
-            e_new[R.j] = val;
+            const Val val = A::finish(R.base, acc, R.dj, identity != 0);
+            const unsigned long long bits = A::to_bits(val);
+            unsigned long long* dst = cl.map_shared_rank(xs, (unsigned)R.j & cmask);
+            dst[(unsigned)R.j >> lg] = bits;
+            reinterpret_cast<unsigned long long*>(e_new)[R.j] = bits;
+            if (out64) out64[R.j] = A::to_double(val);
         }
     };
     Row cur;
@@ -651,8 +742,8 @@ int sweep_form_setting() { return g_sweep_form.load(std::memory_order_relaxed); 
 // Launch of the cluster form; false (nothing launched) when the cluster does not fit.
 template <typename MT, bool FWD>
 static bool launch_sweep_cluster(const SpArgs& a, const double* r, const double* eold, double* enew,
-                                 int identity, int check, int nparts, int64_t nl, cudaStream_t st,
-                                 lsq_status& status) {
+                                 double* out64, int identity, int check, int nparts, int64_t nl,
+                                 cudaStream_t st, lsq_status& status) {
     static std::atomic<int> fits{-1};   // per kernel instance: the cluster fits on this device
     auto kern = k_sp_sweep_cl<MT, FWD>;
     const int C = 1 << SC_LG;
@@ -686,7 +777,7 @@ static bool launch_sweep_cluster(const SpArgs& a, const double* r, const double*
     }
     if (!f) return false;
     const int lg = SC_LG;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, r, eold, enew, identity, check, nparts, nl, lg);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, r, eold, enew, out64, identity, check, nparts, nl, lg);
     count_launch();
     status = e == cudaSuccess ? LSQ_OK : LSQ_ERR_CUDA;
     if (e != cudaSuccess) set_error(std::string("cluster sweep launch: ") + cudaGetErrorString(e));
@@ -697,7 +788,7 @@ static bool launch_sweep_cluster(const SpArgs& a, const double* r, const double*
 // the level waits to end), or the one-CTA or one-cluster form when the schedule calls for it.
 template <typename MT, bool FWD>
 static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* eold, double* enew,
-                               int identity, int check, int nparts, int idx, cudaStream_t st) {
+                               double* out64, int identity, int check, int nparts, int idx, cudaStream_t st) {
     static std::atomic<int> grid_cache{0};   // one per kernel instance; callers may be threads
     auto kern = k_sp_sweep_vf<MT, FWD>;
     int grid = grid_cache.load(std::memory_order_relaxed);
@@ -712,7 +803,7 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
     }
     const int64_t nl = FWD ? a.one_f : a.one_b;
     if (nl > 0) {   // deep, narrow level structure: the whole sweep in one CTA
-        k_sp_sweep_1cta<MT, FWD><<<1, S1_T, 0, st>>>(a, r, eold, enew, identity, check, nparts, nl);
+        k_sp_sweep_1cta<MT, FWD><<<1, S1_T, 0, st>>>(a, r, eold, enew, out64, identity, check, nparts, nl);
         count_launch();
         LSQ_CUDA(cudaGetLastError());
         return LSQ_OK;
@@ -720,14 +811,14 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
     const int64_t ncl = FWD ? a.cl_f : a.cl_b;
     if (ncl > 0) {   // deep levels of moderate width, the vector within a cluster's shared memory
         lsq_status q = LSQ_OK;
-        if (launch_sweep_cluster<MT, FWD>(a, r, eold, enew, identity, check, nparts, ncl, st, q)) return q;
+        if (launch_sweep_cluster<MT, FWD>(a, r, eold, enew, out64, identity, check, nparts, ncl, st, q)) return q;
     }
     // the grid form: fill e_new with the empty marker, then the value-flag sweep
     k_fill_empty<<<(unsigned)std::min<int64_t>((a.n + SP_T - 1) / SP_T, 152 * 8), SP_T, 0, st>>>(enew, a.n);
     count_launch();
     (void)idx;
     SpArgs av = a;
-    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &check, &nparts};
+    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, (void*)&out64, &identity, &check, &nparts};
     const int g_sweep = sweep_grid(grid, a.n, FWD ? a.nlev_f : a.nlev_b, SP_T / 32);
     LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(g_sweep), dim3(SP_T), params, 0, st));
     count_launch();
@@ -830,14 +921,18 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     };
     // z = P g with t forward and t backward sweeps; epoch advanced per sweep
     lsq_status sweep_status = LSQ_OK;
-    auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int check, int idx) {
+    // FP32 M: the sweeps keep their vectors as float pairs in e0/e1 and the last one also writes
+    // z in FP64; FP64 M: the last sweep writes z directly
+    const bool pairs = P->op_dtype == LSQ_F32;
+    auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, double* out64, int identity,
+                     int check, int idx) {
         lsq_status q;
-        if (P->op_dtype == LSQ_F32)
-            q = fwd ? launch_sweep<float, true>(a, r, eold, enew, identity, check, gvec, idx, st)
-                    : launch_sweep<float, false>(a, r, eold, enew, identity, check, gvec, idx, st);
+        if (pairs)
+            q = fwd ? launch_sweep<float, true>(a, r, eold, enew, out64, identity, check, gvec, idx, st)
+                    : launch_sweep<float, false>(a, r, eold, enew, out64, identity, check, gvec, idx, st);
         else
-            q = fwd ? launch_sweep<double, true>(a, r, eold, enew, identity, check, gvec, idx, st)
-                    : launch_sweep<double, false>(a, r, eold, enew, identity, check, gvec, idx, st);
+            q = fwd ? launch_sweep<double, true>(a, r, eold, enew, out64, identity, check, gvec, idx, st)
+                    : launch_sweep<double, false>(a, r, eold, enew, out64, identity, check, gvec, idx, st);
         if (q != LSQ_OK) sweep_status = q;
     };
     // z = P g: t forward then t backward sweeps (the first may carry the convergence check)
@@ -851,13 +946,14 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         double* bufs[2] = {a.e0, a.e1};
         int cur = 0, idx = 0;
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            sweep(true, a.g, eold, bufs[cur], 0, (t == 0) ? check : 0, idx);
+            sweep(true, a.g, eold, bufs[cur], nullptr, 0, (t == 0) ? check : 0, idx);
             eold = bufs[cur];
             cur ^= 1;
         }
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            double* dst = (t == P->sweeps - 1) ? a.z : bufs[cur];
-            sweep(false, a.g, eold, dst, (P->sweeps == 1) ? 1 : 0, 0, idx);
+            const bool last = t == P->sweeps - 1;
+            double* dst = (last && !pairs) ? a.z : bufs[cur];
+            sweep(false, a.g, eold, dst, (last && pairs) ? a.z : nullptr, (P->sweeps == 1) ? 1 : 0, 0, idx);
             eold = dst;
             cur ^= 1;
         }
@@ -1025,20 +1121,24 @@ lsq_status sparse_apply(const lsq_precond* P, const double* r, double* e, int64_
         const double* eold = nullptr;
         double* bufs[2] = {a.e0, a.e1};
         int cur = 0, idx = 0;
+        // FP32 M: float pairs in e0/e1, the last sweep also writes out in FP64
+        const bool pairs = P->op_dtype == LSQ_F32;
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            lsq_status q = P->op_dtype == LSQ_F32
-                ? launch_sweep<float, true>(a, rc, eold, bufs[cur], 0, 0, 0, idx, st)
-                : launch_sweep<double, true>(a, rc, eold, bufs[cur], 0, 0, 0, idx, st);
+            lsq_status q = pairs
+                ? launch_sweep<float, true>(a, rc, eold, bufs[cur], nullptr, 0, 0, 0, idx, st)
+                : launch_sweep<double, true>(a, rc, eold, bufs[cur], nullptr, 0, 0, 0, idx, st);
             if (q != LSQ_OK) return q;
             eold = bufs[cur];
             cur ^= 1;
         }
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            double* dst = (t == P->sweeps - 1) ? out : bufs[cur];
+            const bool last = t == P->sweeps - 1;
+            double* dst = (last && !pairs) ? out : bufs[cur];
+            double* out64 = (last && pairs) ? out : nullptr;
             const int ident = P->sweeps == 1 ? 1 : 0;
-            lsq_status q = P->op_dtype == LSQ_F32
-                ? launch_sweep<float, false>(a, rc, eold, dst, ident, 0, 0, idx, st)
-                : launch_sweep<double, false>(a, rc, eold, dst, ident, 0, 0, idx, st);
+            lsq_status q = pairs
+                ? launch_sweep<float, false>(a, rc, eold, dst, out64, ident, 0, 0, idx, st)
+                : launch_sweep<double, false>(a, rc, eold, dst, out64, ident, 0, 0, idx, st);
             if (q != LSQ_OK) return q;
             eold = dst;
             cur ^= 1;

@@ -430,3 +430,46 @@ def test_block_cluster_sweep_matches_oracle(lsq, orc, sweep_form, case, k, sweep
         assert_solution(X3[c], y / smp.d, kappa, f"cluster block {case} column {c}")
         assert_iterations(i3.iters[c], oi["iters"], _variants(orc, seen, smp, Mo, b[c], o),
                           f"cluster block {case} t={sweeps} column {c}")
+
+
+def _sgs_reference(M, r, sweeps):
+    """Alg. 3 in FP64 with scipy's triangular solves on the given sparse M: t forward sweeps
+    e <- e + (D + L)^{-1} (r - M e), then t backward sweeps with (D + U), from e = 0."""
+    import scipy.sparse as sps
+    from scipy.sparse.linalg import spsolve_triangular
+    lower = sps.tril(M, format="csr")
+    upper = sps.triu(M, format="csr")
+    e = np.zeros_like(r)
+    for _ in range(sweeps):
+        e = e + spsolve_triangular(lower, r - M @ e, lower=True)
+    for _ in range(sweeps):
+        e = e + spsolve_triangular(upper, r - M @ e, lower=False)
+    return e
+
+
+@pytest.mark.parametrize("sweeps", [1, 2])
+@pytest.mark.parametrize("case", ["sprand", "graph", "wide", "mid", "graph_wide"])
+def test_fp32_m_sweeps_in_float_pairs(lsq, orc, sweep_form, case, sweeps):
+    """FP32 M (the precision form): the sweeps sum in double-float on the FP32 units.  Every
+    form gives the same bits, and the result matches Alg. 3 in FP64 on the same matrix (the
+    FP32-rounded off-diagonal entries, the FP64 diagonal; scipy triangular solves) to 1e-10:
+    the double-float sums keep ~48 bits."""
+    import scipy.sparse as sps
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 1003, sweeps=sweeps, pdt=1)
+    rp, ci, va = (t.cpu().numpy() for t in P.M_csr())
+    n = seen["n"]
+    # the sweeps use the FP32-rounded off-diagonal entries and the FP64 reciprocal diagonal
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    v = np.where(rows == ci, va, va.astype(np.float32).astype(np.float64))
+    M32 = sps.csr_matrix((v, ci, rp), shape=(n, n))
+    R = np.random.default_rng(9 + sweeps).standard_normal((2, n))
+    Rt = torch.from_numpy(R).cuda()
+    outs = {}
+    for form in (1, 2, 3):
+        sweep_form(form)
+        outs[form] = P.apply(Rt).cpu().numpy()
+    assert np.array_equal(outs[1], outs[2]), "grid and one-CTA sweeps differ"
+    assert np.array_equal(outs[1], outs[3]), "grid and cluster sweeps differ"
+    for c in range(2):
+        ref = _sgs_reference(M32, R[c], sweeps)
+        assert rel(outs[1][c], ref) <= 1e-10, (case, c, rel(outs[1][c], ref))

@@ -60,6 +60,7 @@ struct SpArgs {
     int sweeps;
     // vectors
     double *y, *g, *z, *p, *pt, *w, *q, *e0, *e1, *h;
+    double* pt2;              // pt as (hi, lo) float pairs for FP32/BF16 row passes, or NULL
     double* part;             // per-block partials: [row pass: rblk][update: nblk][g^T z: nblk]
     int nblk;                 // blocks of the vector kernels
     int rblk;                 // capacity for the row pass's blocks
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_re
     __shared__ double sh[40];
     if (a.S->done) return;
     const void* vals = use_res ? a.vals_res : a.vals;
+    const bool pairs = mode == SPM_MATVEC && !use_res && a.pt2 != nullptr && x == a.pt;
     const int L = a.lpr;
     const int sub = threadIdx.x & (L - 1);
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
@@ -115,39 +117,89 @@ __global__ void __launch_bounds__(SP_T) k_sp_rows(SpArgs a, int mode, int use_re
 #pragma unroll
         for (int r = 0; r < 5; ++r) rp[r] = a.row_ptr[min(i0 + r, a.m)];
         double dot[4] = {0.0, 0.0, 0.0, 0.0};
-        if (mode != SPM_RHS) {
-            // the 4 rows' entries are contiguous: walk them flat, 4 per lane at a time, all
-            // loads (and then all gathers) of a step in flight together; each entry goes to
-            // its row's sum, every row still summing its entries in order per lane
+        // FP32 or BF16 values times the float-pair copy of x: double-float sums on the FP32
+        // units (the FP64 unit would take ~64 cycles per dependent step); one conversion to
+        // FP64 per row
+        constexpr bool PAIR_OK = DT == LSQ_F32 || DT == LSQ_BF16;
+        if (PAIR_OK && pairs) {
+            f2 ds[4] = {f2{0.f, 0.f}, f2{0.f, 0.f}, f2{0.f, 0.f}, f2{0.f, 0.f}};
+            const unsigned long long* x2 = reinterpret_cast<const unsigned long long*>(a.pt2);
             for (int64_t e0 = rp[0] + sub; e0 < rp[4]; e0 += 4 * L) {
-                double av[4];
+                float av[4];
                 int32_t cv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int64_t e = e0 + (int64_t)u * L;
                     const bool in = e < rp[4];
-                    av[u] = in ? (double)Val<DT>::load(vals, e) : 0.0;
+                    av[u] = in ? (float)Val<DT>::load(vals, e) : 0.f;
                     cv[u] = in ? a.col_idx[e] : -1;
                 }
-                double xv[4];
+                unsigned long long xb[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) xv[u] = cv[u] >= 0 ? x[cv[u]] : 0.0;
+                for (int u = 0; u < 4; ++u) xb[u] = cv[u] >= 0 ? x2[cv[u]] : 0ull;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int64_t e = e0 + (int64_t)u * L;
                     if (cv[u] >= 0) {
                         const int r = (e >= rp[1]) + (e >= rp[2]) + (e >= rp[3]);
-                        if (r == 0) dot[0] = fma(av[u], xv[u], dot[0]);
-                        else if (r == 1) dot[1] = fma(av[u], xv[u], dot[1]);
-                        else if (r == 2) dot[2] = fma(av[u], xv[u], dot[2]);
-                        else dot[3] = fma(av[u], xv[u], dot[3]);
+                        const f2 xv = f2{__uint_as_float((unsigned)xb[u]), __uint_as_float((unsigned)(xb[u] >> 32))};
+                        float pp, pe;
+                        two_prod(av[u], xv.hi, pp, pe);
+                        pe = fmaf(av[u], xv.lo, pe);
+                        auto add = [&](f2& d) {
+                            float s1, e1;
+                            two_sum(d.hi, pp, s1, e1);
+                            d.hi = s1;
+                            d.lo += e1 + pe;
+                        };
+                        if (r == 0) add(ds[0]);
+                        else if (r == 1) add(ds[1]);
+                        else if (r == 2) add(ds[2]);
+                        else add(ds[3]);
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            for (int o = L >> 1; o > 0; o >>= 1) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], o);
+            for (int r = 0; r < 4; ++r) {
+                f2 v = df_norm(ds[r]);
+                for (int o = L >> 1; o > 0; o >>= 1) df_add(v, df_shfl_xor(v, o));
+                dot[r] = sub == 0 ? df_to_double(v) : 0.0;
+            }
+        } else {
+            if (mode != SPM_RHS) {
+                // the 4 rows' entries are contiguous: walk them flat, 4 per lane at a time, all
+                // loads (and then all gathers) of a step in flight together; each entry goes to
+                // its row's sum, every row still summing its entries in order per lane
+                for (int64_t e0 = rp[0] + sub; e0 < rp[4]; e0 += 4 * L) {
+                    double av[4];
+                    int32_t cv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t e = e0 + (int64_t)u * L;
+                        const bool in = e < rp[4];
+                        av[u] = in ? (double)Val<DT>::load(vals, e) : 0.0;
+                        cv[u] = in ? a.col_idx[e] : -1;
+                    }
+                    double xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xv[u] = cv[u] >= 0 ? x[cv[u]] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t e = e0 + (int64_t)u * L;
+                        if (cv[u] >= 0) {
+                            const int r = (e >= rp[1]) + (e >= rp[2]) + (e >= rp[3]);
+                            if (r == 0) dot[0] = fma(av[u], xv[u], dot[0]);
+                            else if (r == 1) dot[1] = fma(av[u], xv[u], dot[1]);
+                            else if (r == 2) dot[2] = fma(av[u], xv[u], dot[2]);
+                            else dot[3] = fma(av[u], xv[u], dot[3]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                for (int o = L >> 1; o > 0; o >>= 1) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], o);
+        }
         if (sub == 0) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -680,7 +732,13 @@ __global__ void __launch_bounds__(SP_T) k_sp_pnext(SpArgs a, int first, int npar
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x) {
         const double pj = first ? a.z[j] : fma(beta, a.p[j], a.z[j]);
         a.p[j] = pj;
-        a.pt[j] = pj * a.inv_d[j];
+        const double ptj = pj * a.inv_d[j];
+        a.pt[j] = ptj;
+        if (a.pt2) {
+            const f2 v = df_from_double(ptj);
+            reinterpret_cast<unsigned long long*>(a.pt2)[j] =
+                (unsigned long long)__float_as_uint(v.hi) | ((unsigned long long)__float_as_uint(v.lo) << 32);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -866,7 +924,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
     size_t o_S = take(sizeof(SpState)), o_vT = take(es * nnz), o_vT64 = take(res64 && DT != LSQ_F64 ? 8 * nnz : 16),
-           o_vec = take(8 * (size_t)n * 10), o_q = take(8 * (size_t)m),
+           o_vec = take(8 * (size_t)n * 11), o_q = take(8 * (size_t)m),
            o_part = take(8 * (size_t)(rblk + 2 * nblk)),
            o_n2 = take(64);
     Scratch sc;
@@ -890,6 +948,7 @@ static lsq_status sp_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     a.y = vec; a.g = vec + n; a.z = vec + 2 * n; a.p = vec + 3 * n; a.pt = vec + 4 * n;
     a.w = vec + 5 * n; a.e0 = vec + 6 * n; a.e1 = vec + 7 * n; a.h = vec + 8 * n;
     double* tmpv = vec + 9 * n;
+    a.pt2 = (DT == LSQ_F32 || DT == LSQ_BF16) ? vec + 10 * n : nullptr;
     a.q = (double*)(base + o_q);
     a.loff_f = SH->loff_f; a.loff_b = SH->loff_b; a.nlev_f = SH->nlev_f; a.nlev_b = SH->nlev_b;
     choose_sweep_form(a, SH, n);

@@ -5,6 +5,9 @@
 #pragma once
 #include "sparse.cuh"
 #include "values.cuh"
+#include "dfloat.cuh"
+
+#include <type_traits>
 
 namespace lsq {
 
@@ -479,11 +482,61 @@ __device__ __forceinline__ void bk_sweep_ep_body(BkArgs a, const double* r, cons
 // added in warp order.  Here a row's K values are published by one flag per row (the sweep's
 // epoch, release) after they are written, so a reader polls one flag per dependency (acquire,
 // batched, bounded) and then loads the values; the flags are cumulative over the solve, so
-// nothing is reset between sweeps.
+// nothing is reset between sweeps.  PAIRS (FP32 M, stream-ordered solves): the sums run in
+// double-float on the FP32 units and the sweep vectors hold (hi, lo) float pairs, with the
+// last sweep also writing FP64 values to out64; otherwise FP64 sums on FP64 vectors.
 constexpr int BK_PFC = 4;
-template <typename MT, bool FWD, int KT>
+__device__ __forceinline__ f2 bk_pair(unsigned long long u) {
+    return f2{__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32))};
+}
+__device__ __forceinline__ unsigned long long bk_bits(f2 v) {
+    return (unsigned long long)__float_as_uint(v.hi) | ((unsigned long long)__float_as_uint(v.lo) << 32);
+}
+// acc += m v (float m, pair v) in the cascaded double-float form
+__device__ __forceinline__ void bk_mad_pair(f2& acc, float m, f2 v) {
+    float p, pe;
+    two_prod(m, v.hi, p, pe);
+    pe = fmaf(m, v.lo, pe);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo += e + pe;
+}
+__device__ __forceinline__ f2 bk_mul_pair(f2 a, f2 b) {
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float hi = p + e;
+    return f2{hi, e - (hi - p)};
+}
+// the pair form of bk_reduce_scatter: lane l ends with the warp total of column l >> (5 - log2 KT)
+template <int KT>
+__device__ __forceinline__ f2 bk_reduce_scatter_pair(f2 (&v)[KT], int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s;
+        const int half = KT >> (s + 1);
+        if (half >= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const f2 send = upper ? v[i] : v[i + half];
+                f2 keep = upper ? v[i + half] : v[i];
+                df_add(keep, df_shfl_xor(send, o));
+                v[i] = keep;
+            }
+        } else {
+            df_add(v[0], df_shfl_xor(v[0], o));
+        }
+    }
+    return v[0];
+}
+template <typename MT, bool FWD, int KT, bool PAIRS = false>
 __device__ __forceinline__ void bk_sweep_cta_body(BkArgs a, const double* r, const double* e_old,
-                                                       double* e_new, int identity, int sweep_idx) {
+                                                       double* e_new, int identity, int sweep_idx,
+                                                       double* out64 = nullptr) {
+    static_assert(!PAIRS || sizeof(MT) == 4, "float pairs need FP32 M");
     __shared__ double s_part[BK_T / 32][KT];
     const int tdir = FWD ? sweep_idx : sweep_idx - a.sweeps;
     const unsigned epoch = (unsigned)((unsigned long long)a.S->napply * a.sweeps + tdir + 1);
@@ -494,32 +547,40 @@ __device__ __forceinline__ void bk_sweep_cta_body(BkArgs a, const double* r, con
     const int K = a.K;
     const bool other = !identity && e_old != nullptr;
     constexpr int SH = (KT >= 32) ? 0 : (KT >= 16 ? 1 : (KT >= 8 ? 2 : (KT >= 4 ? 3 : (KT >= 2 ? 4 : 5))));
+    typedef typename std::conditional<PAIRS, f2, double>::type Acc;
+    const unsigned long long* eold_u = reinterpret_cast<const unsigned long long*>(e_old);
+    const unsigned long long* enew_u = reinterpret_cast<const unsigned long long*>(e_new);
     for (int64_t slot = blockIdx.x; slot < a.n; slot += gridDim.x) {
         const int64_t j = sched[slot];
         const int64_t e0 = a.mptr[j], e1 = a.mptr[j + 1], ed = a.mdiag[j];
         const int64_t d0 = FWD ? e0 : ed + 1, d1 = FWD ? ed : e1;
         const int64_t o0 = FWD ? ed + 1 : e0, o1 = FWD ? e1 : ed;
-        double acc[KT];
+        Acc acc[KT];
 #pragma unroll
-        for (int c = 0; c < KT; ++c) acc[c] = 0.0;
+        for (int c = 0; c < KT; ++c) {
+            if constexpr (PAIRS) acc[c] = f2{0.f, 0.f};
+            else acc[c] = 0.0;
+        }
         if (other)
             for (int64_t e = o0 + tid; e < o1; e += BK_T) {
                 const int64_t k = a.mcol[e];
-                const double mk = (double)mv[e];
 #pragma unroll
                 for (int c = 0; c < KT; ++c)
-                    if (c < K) acc[c] = fma(mk, e_old[k * K + c], acc[c]);
+                    if (c < K) {
+                        if constexpr (PAIRS) bk_mad_pair(acc[c], (float)mv[e], bk_pair(eold_u[k * K + c]));
+                        else acc[c] = fma((double)mv[e], e_old[k * K + c], acc[c]);
+                    }
             }
         for (int64_t base = d0 + tid; base < d1; base += BK_T * BK_PFC) {
             int32_t kk[BK_PFC];
-            double mm[BK_PFC];
+            MT mm[BK_PFC];
             unsigned f[BK_PFC];
 #pragma unroll
             for (int u = 0; u < BK_PFC; ++u) {
                 const int64_t e = base + (int64_t)BK_T * u;
                 kk[u] = -1;
-                mm[u] = 0.0;
-                if (e < d1) { kk[u] = a.mcol[e]; mm[u] = (double)mv[e]; }
+                mm[u] = MT(0);
+                if (e < d1) { kk[u] = a.mcol[e]; mm[u] = mv[e]; }
             }
 #pragma unroll
             for (int u = 0; u < BK_PFC; ++u) f[u] = kk[u] >= 0 ? bk_ld_acquire_u32(flag + kk[u]) : epoch;
@@ -542,24 +603,59 @@ __device__ __forceinline__ void bk_sweep_cta_body(BkArgs a, const double* r, con
 #pragma unroll
             for (int u = 0; u < BK_PFC; ++u) {
                 if (kk[u] >= 0) {
-                    const double* row = e_new + (int64_t)kk[u] * K;
+                    if constexpr (PAIRS) {
+                        const unsigned long long* row = enew_u + (int64_t)kk[u] * K;
 #pragma unroll
-                    for (int c = 0; c < KT; ++c)
-                        if (c < K) acc[c] = fma(mm[u], __ldcg(row + c), acc[c]);
+                        for (int c = 0; c < KT; ++c)
+                            if (c < K) bk_mad_pair(acc[c], (float)mm[u], bk_pair(__ldcg(row + c)));
+                    } else {
+                        const double* row = e_new + (int64_t)kk[u] * K;
+#pragma unroll
+                        for (int c = 0; c < KT; ++c)
+                            if (c < K) acc[c] = fma((double)mm[u], __ldcg(row + c), acc[c]);
+                    }
                 }
             }
         }
-        const double tot = bk_reduce_scatter<KT>(acc, lane);
-        if ((lane & ((1 << SH) - 1)) == 0) s_part[wid][lane >> SH] = tot;
+        if constexpr (PAIRS) {
+#pragma unroll
+            for (int c = 0; c < KT; ++c) acc[c] = df_norm(acc[c]);
+            const f2 tot = bk_reduce_scatter_pair<KT>(acc, lane);
+            if ((lane & ((1 << SH) - 1)) == 0)
+                reinterpret_cast<unsigned long long*>(&s_part[wid][0])[lane >> SH] = bk_bits(tot);
+        } else {
+            const double tot = bk_reduce_scatter<KT>(acc, lane);
+            if ((lane & ((1 << SH) - 1)) == 0) s_part[wid][lane >> SH] = tot;
+        }
         __syncthreads();
         if (wid == 0) {
             if (lane < K) {
-                double sum = 0.0;
-#pragma unroll
-                for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][lane];
                 const double dj = a.dinv[j];
                 const int64_t at = j * K + lane;
-                e_new[at] = identity ? e_old[at] - sum * dj : (r[at] - sum) * dj;
+                if constexpr (PAIRS) {
+                    f2 sum{0.f, 0.f};
+#pragma unroll
+                    for (int w = 0; w < BK_T / 32; ++w)
+                        df_add(sum, bk_pair(reinterpret_cast<const unsigned long long*>(&s_part[w][0])[lane]));
+                    const f2 djp = df_from_double(dj);
+                    f2 v;
+                    if (identity) {
+                        v = bk_pair(eold_u[at]);
+                        const f2 t = bk_mul_pair(sum, djp);
+                        df_add(v, f2{-t.hi, -t.lo});
+                    } else {
+                        f2 b = df_from_double(r[at]);
+                        df_add(b, f2{-sum.hi, -sum.lo});
+                        v = bk_mul_pair(b, djp);
+                    }
+                    reinterpret_cast<unsigned long long*>(e_new)[at] = bk_bits(v);
+                    if (out64) out64[at] = df_to_double(v);
+                } else {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < BK_T / 32; ++w) sum += s_part[w][lane];
+                    e_new[at] = identity ? e_old[at] - sum * dj : (r[at] - sum) * dj;
+                }
             }
             __syncwarp();
             if (lane == 0) bk_st_release_u32(flag + j, epoch);

@@ -53,25 +53,29 @@ __global__ void k_bk_fill_empty(double* e, int64_t cnt) {
     bk_fill_empty_body(e, cnt);
 }
 
+// every block sweep kernel takes the same arguments (one launch path); out64 is used by the
+// pair form of the CTA-per-row sweep only
 template <typename MT, bool FWD>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep(BkArgs a, const double* r, const double* e_old,
-                                                   double* e_new, int identity, int sweep_idx) {
+                                                   double* e_new, int identity, int sweep_idx, double* out64) {
     if (a.S->done) return;
     bk_sweep_body<MT, FWD>(a, r, e_old, e_new, identity, sweep_idx);
+    (void)out64;
 }
 
 template <typename MT, bool FWD, int KT>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep_ep(BkArgs a, const double* r, const double* e_old,
-                                                      double* e_new, int identity, int sweep_idx) {
+                                                      double* e_new, int identity, int sweep_idx, double* out64) {
     if (a.S->done) return;
     bk_sweep_ep_body<MT, FWD, KT>(a, r, e_old, e_new, identity, sweep_idx);
+    (void)out64;
 }
 
-template <typename MT, bool FWD, int KT>
+template <typename MT, bool FWD, int KT, bool PAIRS>
 __global__ void __launch_bounds__(BK_T) k_bk_sweep_cta(BkArgs a, const double* r, const double* e_old,
-                                                       double* e_new, int identity, int sweep_idx) {
+                                                       double* e_new, int identity, int sweep_idx, double* out64) {
     if (a.S->done) return;
-    bk_sweep_cta_body<MT, FWD, KT>(a, r, e_old, e_new, identity, sweep_idx);
+    bk_sweep_cta_body<MT, FWD, KT, PAIRS>(a, r, e_old, e_new, identity, sweep_idx, out64);
 }
 
 // The CTA-per-row sweep in ONE thread-block cluster of C = 2^lg CTAs, for deep level
@@ -241,8 +245,8 @@ static unsigned bk_grid(int64_t work, int64_t cap) {
 // Cooperative launch: every warp of the sweep must be resident for the level waits to end.
 // The grid (SMs x resident blocks) is computed once per kernel.
 static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const double* r, const double* eold,
-                                  double* enew, int identity, int idx, int64_t nlev, int units_per_block,
-                                  cudaStream_t st) {
+                                  double* enew, double* out64, int identity, int idx, int64_t nlev,
+                                  int units_per_block, cudaStream_t st) {
     static std::mutex mu;
     static std::unordered_map<const void*, int> grids;
     int grid = 0;
@@ -265,7 +269,7 @@ static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const doubl
     k_bk_fill_empty<<<(unsigned)std::min<int64_t>((cnt + BK_T - 1) / BK_T, 152 * 8), BK_T, 0, st>>>(enew, cnt);
     count_launch();
     BkArgs av = a;
-    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &idx};
+    void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, &identity, &idx, (void*)&out64};
     const int g_sweep = sweep_grid(grid, a.n, nlev, units_per_block);
     LSQ_CUDA(cudaLaunchCooperativeKernel(kern, dim3(g_sweep), dim3(BK_T), params, 0, st));
     count_launch();
@@ -273,8 +277,9 @@ static lsq_status bk_launch_sweep(const void* kern, const BkArgs& a, const doubl
 }
 
 // lane-per-column sweep for short rows, entry-parallel sweep (KT >= K accumulators) for long
-// mode 0: lane per column (short rows); 1: warp per row, lane per entry; 2: CTA per row
-template <typename MT, bool FWD>
+// mode 0: lane per column (short rows); 1: warp per row, lane per entry; 2: CTA per row (with
+// float-pair sums when PAIRS)
+template <typename MT, bool FWD, bool PAIRS = false>
 static const void* bk_sweep_kernel(int mode, int K) {
     if (mode == 0) return (const void*)k_bk_sweep<MT, FWD>;
     if (mode == 1) {
@@ -284,11 +289,11 @@ static const void* bk_sweep_kernel(int mode, int K) {
         if (K <= 16) return (const void*)k_bk_sweep_ep<MT, FWD, 16>;
         return (const void*)k_bk_sweep_ep<MT, FWD, 32>;
     }
-    if (K <= 2) return (const void*)k_bk_sweep_cta<MT, FWD, 2>;
-    if (K <= 4) return (const void*)k_bk_sweep_cta<MT, FWD, 4>;
-    if (K <= 8) return (const void*)k_bk_sweep_cta<MT, FWD, 8>;
-    if (K <= 16) return (const void*)k_bk_sweep_cta<MT, FWD, 16>;
-    return (const void*)k_bk_sweep_cta<MT, FWD, 32>;
+    if (K <= 2) return (const void*)k_bk_sweep_cta<MT, FWD, 2, PAIRS>;
+    if (K <= 4) return (const void*)k_bk_sweep_cta<MT, FWD, 4, PAIRS>;
+    if (K <= 8) return (const void*)k_bk_sweep_cta<MT, FWD, 8, PAIRS>;
+    if (K <= 16) return (const void*)k_bk_sweep_cta<MT, FWD, 16, PAIRS>;
+    return (const void*)k_bk_sweep_cta<MT, FWD, 32, PAIRS>;
 }
 
 template <typename MT, bool FWD>
@@ -442,8 +447,6 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     const double dep = (double)(SH->nnz_M - n) / (2.0 * (double)n);
     const int smode = dep > 96.0 ? 2 : (dep > 24.0 ? 1 : 0);
     const bool m32 = P->op_dtype == LSQ_F32;
-    const void* kf = m32 ? bk_sweep_kernel<float, true>(smode, K) : bk_sweep_kernel<double, true>(smode, K);
-    const void* kb = m32 ? bk_sweep_kernel<float, false>(smode, K) : bk_sweep_kernel<double, false>(smode, K);
     // one cluster on request (lsq_set_sweep_form 3) where the block vector fits in the
     // cluster's shared memory; the stream-ordered solve only (the persistent kernel keeps the
     // grid forms).  Never chosen by shape: on the 1e6 x 1e4 workload with 16 columns (1227
@@ -458,13 +461,22 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
     };
     const bool cl_f = want_cl(SH->nlev_f) && bk_cluster_fits(cf);
     const bool cl_b = want_cl(SH->nlev_b) && bk_cluster_fits(cb);
+    // FP32 M with the CTA-per-row form: double-float sums on float-pair sweep vectors, the
+    // last sweep also writing z in FP64 (a dependent FP64 step costs ~64 cycles on GB300);
+    // the cluster and persistent forms keep FP64 sums
+    const bool pairs = m32 && smode == 2 && !cl_f && !cl_b;
+    const void* kf = pairs ? bk_sweep_kernel<float, true, true>(smode, K)
+                           : (m32 ? bk_sweep_kernel<float, true>(smode, K) : bk_sweep_kernel<double, true>(smode, K));
+    const void* kb = pairs ? bk_sweep_kernel<float, false, true>(smode, K)
+                           : (m32 ? bk_sweep_kernel<float, false>(smode, K) : bk_sweep_kernel<double, false>(smode, K));
     lsq_status sweep_status = LSQ_OK;
-    auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, int identity, int idx) {
+    auto sweep = [&](bool fwd, const double* r, const double* eold, double* enew, double* out64, int identity,
+                     int idx) {
         lsq_status q;
         if (fwd && cl_f) q = bk_launch_sweep_cl(cf, a, r, eold, enew, identity, SH->loff_f, SH->nlev_f, st);
         else if (!fwd && cl_b) q = bk_launch_sweep_cl(cb, a, r, eold, enew, identity, SH->loff_b, SH->nlev_b, st);
-        else q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, identity, idx, fwd ? SH->nlev_f : SH->nlev_b,
-                                 smode == 2 ? 1 : BK_T / 32, st);
+        else q = bk_launch_sweep(fwd ? kf : kb, a, r, eold, enew, out64, identity, idx,
+                                 fwd ? SH->nlev_f : SH->nlev_b, smode == 2 ? 1 : BK_T / 32, st);
         if (q != LSQ_OK) sweep_status = q;
     };
     // z = P g: t forward then t backward sweeps
@@ -481,13 +493,14 @@ static lsq_status bk_solve_impl(const lsq_matrix* A, const lsq_precond* P, const
         double* bufs[2] = {a.e0, a.e1};
         int cur = 0, idx = 0;
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            sweep(true, a.g, eold, bufs[cur], 0, idx);
+            sweep(true, a.g, eold, bufs[cur], nullptr, 0, idx);
             eold = bufs[cur];
             cur ^= 1;
         }
         for (int t = 0; t < P->sweeps; ++t, ++idx) {
-            double* dst = (t == P->sweeps - 1) ? a.z : bufs[cur];
-            sweep(false, a.g, eold, dst, (P->sweeps == 1) ? 1 : 0, idx);
+            const bool last = t == P->sweeps - 1;
+            double* dst = (last && !pairs) ? a.z : bufs[cur];
+            sweep(false, a.g, eold, dst, (last && pairs) ? a.z : nullptr, (P->sweeps == 1) ? 1 : 0, idx);
             eold = dst;
             cur ^= 1;
         }

@@ -473,3 +473,31 @@ def test_fp32_m_sweeps_in_float_pairs(lsq, orc, sweep_form, case, sweeps):
     for c in range(2):
         ref = _sgs_reference(M32, R[c], sweeps)
         assert rel(outs[1][c], ref) <= 1e-10, (case, c, rel(outs[1][c], ref))
+
+
+@pytest.mark.parametrize("case,k,sweeps", [("sprand", 4, 1), ("sprand", 3, 2), ("wide", 16, 1), ("wide", 5, 2)])
+def test_block_fp32_m_cta_sweeps_in_float_pairs(lsq, orc, case, k, sweeps):
+    """FP32 M with the CTA-per-row block sweep (rows of more than 96 dependency entries): the
+    sweeps sum in double-float on float-pair vectors.  Whole solves against the oracle (on the
+    FP64 M: the FP32 operator only changes the preconditioner, and both solves meet the
+    tolerance), and against the same block through the persistent kernel, whose sweeps keep
+    FP64 sums."""
+    Mx, keep, seen, o, P, smp, Mo = _setup(lsq, orc, CASES[case](), 4242, sweeps=sweeps, pdt=1)
+    xs, b = W.rhs_for(seen, k, 1e-3, 4243)
+    B = torch.from_numpy(b).cuda()
+    X, info = lsq.lsq_pcg_solve(Mx, P, B, o)
+    X = X.cpu().numpy()
+    assert (int(info.nnz_M) - seen["n"]) / (2.0 * seen["n"]) > 96.0   # the CTA-per-row form
+    kappa = np.linalg.cond(W.dense_from_csr(seen) / smp.d)
+    for c in sorted({0, k - 1}):
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=o.max_outer, sweeps=sweeps)
+        assert info.converged[c] == 1 and oi["converged"] == 1 and info.relres_true[c] <= o.tol
+        assert_solution(X[c], y / smp.d, kappa, f"FP32 M block {case} column {c}")
+    # the same block through the persistent kernel (the same FP32 M, FP64 sums): the same
+    # solution within the bar and the same iteration counts within 2
+    o.device_loop = 1
+    Xp, ip = lsq.lsq_pcg_solve(Mx, P, B, o)
+    for c in range(k):
+        assert ip.converged[c] == 1
+        assert_solution(X[c], Xp[c].cpu().numpy(), kappa, f"pairs vs persistent column {c}")
+        assert abs(int(info.iters[c]) - int(ip.iters[c])) <= 2, (c, info.iters[c], ip.iters[c])

@@ -343,6 +343,7 @@ constexpr unsigned long long SWEEP_EMPTY = 0xFFF7DEADBEEFCAFEull;
 constexpr int SWG = 8;                 // dependency values a lane loads before it polls
 constexpr unsigned SW_SPIN = 4;        // polls before the first back-off
 constexpr unsigned SW_NS_CAP = 256;    // longest back-off between polls (ns)
+constexpr int SW_T = 256;              // threads per block of the grid sweep
 __global__ void k_fill_empty(double* e, int64_t n) {
     unsigned long long* u = reinterpret_cast<unsigned long long*>(e);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -357,7 +358,7 @@ __device__ __forceinline__ void st_volatile_u64(double* p, unsigned long long v)
     asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 template <typename MT, bool FWD>
-__global__ void __launch_bounds__(SP_T) k_sp_sweep_vf(SpArgs a, const double* r, const double* e_old,
+__global__ void __launch_bounds__(SW_T) k_sp_sweep_vf(SpArgs a, const double* r, const double* e_old,
                                                       double* e_new, double* out64, int identity, int check,
                                                       int nparts) {
     typedef SwArith<MT> A;
@@ -854,7 +855,7 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
         int dev = 0, sms = 0, per = 0;
         LSQ_CUDA(cudaGetDevice(&dev));
         LSQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SP_T, 0));
+        LSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SW_T, 0));
         if (per < 1) { set_error("sweep kernel does not fit on an SM"); return LSQ_ERR_CUDA; }
         grid = sms * per;
         grid_cache.store(grid, std::memory_order_relaxed);
@@ -877,8 +878,8 @@ static lsq_status launch_sweep(const SpArgs& a, const double* r, const double* e
     (void)idx;
     SpArgs av = a;
     void* params[] = {&av, (void*)&r, (void*)&eold, (void*)&enew, (void*)&out64, &identity, &check, &nparts};
-    const int g_sweep = sweep_grid(grid, a.n, FWD ? a.nlev_f : a.nlev_b, SP_T / 32);
-    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(g_sweep), dim3(SP_T), params, 0, st));
+    const int g_sweep = sweep_grid(grid, a.n, FWD ? a.nlev_f : a.nlev_b, SW_T / 32);
+    LSQ_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(g_sweep), dim3(SW_T), params, 0, st));
     count_launch();
     return LSQ_OK;
 }

@@ -395,16 +395,20 @@ __global__ void __launch_bounds__(SW_T) k_sp_sweep_vf(SpArgs a, const double* r,
         unsigned long long u[SWG];
 #pragma unroll
         for (int c = 0; c < SWG; ++c) u[c] = kk[c] >= 0 ? ld_volatile_u64(e_new + kk[c]) : 0ull;
+        // the warp polls as one: it leaves the loop when no lane misses a value, so it comes
+        // out converged (a warp that left lane by lane ran its shuffle reduction ~7x slower)
         unsigned polls = 0, ns = 32;
         while (true) {
             bool missing = false;
 #pragma unroll
             for (int c = 0; c < SWG; ++c) missing = missing || (kk[c] >= 0 && u[c] == SWEEP_EMPTY);
-            if (!missing) break;
+            if (!__any_sync(0xffffffffu, missing)) break;
             ++polls;
-            if (polls > a.max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
+            const bool give_up = polls > a.max_polls ||
+                                 ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u);
+            if (__any_sync(0xffffffffu, give_up)) {
                 ok = false;
-                atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+                if (lane == 0) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
 #pragma unroll
                 for (int c = 0; c < SWG; ++c) if (u[c] == SWEEP_EMPTY) u[c] = 0ull;
                 break;
@@ -428,12 +432,14 @@ __global__ void __launch_bounds__(SW_T) k_sp_sweep_vf(SpArgs a, const double* r,
             for (int64_t e = o0 + lane; e < o1; e += 32) A::mad(acc, mv[e], A::load(e_old, a.mcol[e]));
         const Val base = identity ? A::load(e_old, j) : A::from_double(r[j]);
         const Val dj = A::from_double(a.dinv[j]);
-        for (int64_t b0 = d0 + lane; b0 < d1; b0 += 32 * SWG) {
+        // batches of 32 SWG entries from a warp-uniform base: every lane runs the same number
+        // of batches (gather's polling is warp-collective); lane l takes entries l, l + 32, ...
+        for (int64_t bb = d0; bb < d1; bb += 32 * SWG) {
             int32_t kk[SWG];
             MT mm[SWG];
 #pragma unroll
             for (int c = 0; c < SWG; ++c) {
-                const int64_t e = b0 + 32 * c;
+                const int64_t e = bb + lane + 32 * c;
                 kk[c] = -1;
                 mm[c] = MT(0);
                 if (e < d1) { kk[c] = a.mcol[e]; mm[c] = mv[e]; }

@@ -571,13 +571,15 @@ __device__ __forceinline__ void bk_sweep_cta_body(BkArgs a, const double* r, con
                         else acc[c] = fma((double)mv[e], e_old[k * K + c], acc[c]);
                     }
             }
-        for (int64_t base = d0 + tid; base < d1; base += BK_T * BK_PFC) {
+        // batches from a CTA-uniform base, polled as a warp (__any_sync), so every warp leaves
+        // the wait converged for its reduce-scatter; thread t still takes entries t, t + BK_T, ...
+        for (int64_t bb = d0; bb < d1; bb += BK_T * BK_PFC) {
             int32_t kk[BK_PFC];
             MT mm[BK_PFC];
             unsigned f[BK_PFC];
 #pragma unroll
             for (int u = 0; u < BK_PFC; ++u) {
-                const int64_t e = base + (int64_t)BK_T * u;
+                const int64_t e = bb + tid + (int64_t)BK_T * u;
                 kk[u] = -1;
                 mm[u] = MT(0);
                 if (e < d1) { kk[u] = a.mcol[e]; mm[u] = mv[e]; }
@@ -589,10 +591,12 @@ __device__ __forceinline__ void bk_sweep_cta_body(BkArgs a, const double* r, con
                 bool missing = false;
 #pragma unroll
                 for (int u = 0; u < BK_PFC; ++u) missing = missing || f[u] < epoch;
-                if (!missing) break;
+                if (!__any_sync(0xffffffffu, missing)) break;
                 ++polls;
-                if (polls > a.max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u)) {
-                    atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
+                const bool give_up = polls > a.max_polls ||
+                                     ((polls & 255u) == 0 && *(volatile unsigned*)&a.S->err != 0u);
+                if (__any_sync(0xffffffffu, give_up)) {
+                    if (lane == 0) atomicOr(&a.S->err, DEV_ERR_TIMEOUT);
                     break;
                 }
                 if (polls > 4) { __nanosleep(ns); ns = ns < 256 ? 2 * ns : 256; }

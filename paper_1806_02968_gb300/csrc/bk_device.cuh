@@ -279,23 +279,27 @@ __device__ __forceinline__ unsigned long long bk_ldv(const double* p) {
 __device__ __forceinline__ void bk_stv(double* p, double v) {
     asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
-// Loads N values (use[i] false: skipped), polling the missing ones until all are written.
+// Loads N values (use[i] false: skipped), polling the missing ones until all are written;
+// called by all 32 lanes of a warp together.
 template <int N>
 __device__ __forceinline__ bool bk_gather_ready(const double* const* ptr, const bool* use, double* out,
                                                 unsigned* err, unsigned max_polls) {
     unsigned long long u[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) u[i] = use[i] ? bk_ldv(ptr[i]) : 0ull;
+    // warp-collective: every lane of the warp calls this together and the warp leaves the wait
+    // as one (__any_sync), converged for the shuffles that follow
     unsigned polls = 0, ns = 32;
     bool ok = true;
     while (true) {
         bool missing = false;
 #pragma unroll
         for (int i = 0; i < N; ++i) missing = missing || (use[i] && u[i] == BK_EMPTY);
-        if (!missing) break;
+        if (!__any_sync(0xffffffffu, missing)) break;
         ++polls;
-        if (polls > max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u)) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
+        const bool give_up = polls > max_polls || ((polls & 255u) == 0 && *(volatile unsigned*)err != 0u);
+        if (__any_sync(0xffffffffu, give_up)) {
+            if ((threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_TIMEOUT);
             ok = false;
 #pragma unroll
             for (int i = 0; i < N; ++i) if (u[i] == BK_EMPTY) u[i] = 0ull;

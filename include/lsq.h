@@ -90,7 +90,8 @@ typedef struct {
                               column-normalised A, i.e. P = I */
     double sample_factor;  /* C in s = ceil(C n ln n) (Alg. 2 step 2); 4.0 */
     int32_t normalize;     /* Alg. 2 step 1 on (1) or off (0); 1 */
-    int32_t precond_dtype; /* LSQ_F64 or LSQ_F32: storage/arithmetic of the SGS operator */
+    int32_t precond_dtype; /* LSQ_F64 or LSQ_F32: storage/arithmetic of the SGS operator (CSR:
+                              with LSQ_F32 the sweeps sum in double-float, ~48 bits) */
     uint64_t seed;         /* Philox key word for the draws of Alg. 1; 0 */
     double inner_tol;      /* refinement form only: relative tolerance of each inner
                               solve; 0 = tol (no separate inner tolerance) */

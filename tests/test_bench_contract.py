@@ -58,3 +58,50 @@ def test_roofline_bytes_of_the_benchmark_launch():
     assert byts == it * per_iter + residual
     assert abs(per_iter / 278.6e-6 / 1e12 - 3.86) < 0.005
     assert flops == it * (4.0 * m * n + 2.0 * n * n) + 2 * 4.0 * m * n
+
+
+def test_sweep_latency_bound_arithmetic():
+    """The sparse lines' `sweep` object: ms per sweep = one preconditioner application over 2t,
+    and the latency bound = levels x (half the SM-to-SM round trip + one dependent L2 load).
+    A fake library and tensor layer stand in for the GPU (no device is touched)."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FakeEvent:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self):
+            FakeTorch.clock += 0.0
+            self.t = FakeTorch.clock
+
+        def elapsed_time(self, other):
+            return 6.0   # ms for the timed applications
+
+    class FakeTorch:
+        clock = 0.0
+        float64 = "f64"
+        cuda = types.SimpleNamespace(synchronize=lambda: None, Event=FakeEvent)
+
+        @staticmethod
+        def randn(n, dtype=None, device=None):
+            return [0.0] * n
+
+    api = types.SimpleNamespace(measure_latency=lambda: {"l2_load_ns": 150.0, "sm_round_trip_ns": 320.0,
+                                                         "cluster_barrier_ns": 190.0, "dsmem_load_ns": 100.0,
+                                                         "sm_round_trip_fenced_ns": 800.0})
+    P = types.SimpleNamespace(apply=lambda R: R)
+    saved = sys.modules.get("torch")
+    sys.modules["torch"] = FakeTorch
+    try:
+        out = bench.sweep_latency_bound(api, P, 40000, 1, 1583, reps=3)
+    finally:
+        if saved is not None:
+            sys.modules["torch"] = saved
+        else:
+            del sys.modules["torch"]
+    assert abs(out["ms_per_sweep"] - 6.0 / 3 / 2) < 1e-12
+    assert abs(out["bound_ms_per_sweep"] - 1583 * (160.0 + 150.0) / 1e6) < 1e-12
+    assert abs(out["frac"] - out["bound_ms_per_sweep"] / out["ms_per_sweep"]) < 1e-12
+    assert out["bound"] == "latency" and out["levels"] == 1583

@@ -14,7 +14,13 @@ process's).  The iteration below follows the same textbook steps as the oracle's
 (Alg. 2 step 4, with the stop test of Sec. 5 on the normalised residual) so that the two
 can be compared: the sharded solve must give the single-process iteration count within
 the ±2 bar, a solution within rounding of the single-process one, and bit-identical
-replicated state on every rank."""
+replicated state on every rank.
+
+The preconditioner's matrix shards the same way (Sec. 3.3): A_s^T A_s = Σ_t â_{i_t}^T
+â_{i_t} / (s p_{i_t}) splits by the rank that owns row i_t, so each rank sums the draws
+that landed in its rows, with the global s and p_i = w_i / W, and one all-reduce of the
+n×n partials (before the zero-diagonal fix, which belongs to the sum) gives the matrix one
+process builds."""
 import os
 import socket
 import sys
@@ -166,3 +172,70 @@ def test_sharded_iteration_matches_one_process(tmp_path, case):
     sv = np.linalg.svd(A / oracle.Sample(mat, seed=17).d, compute_uv=False)
     kappa = sv[0] / sv[-1]
     assert np.linalg.norm(ys[0] - y1) / np.linalg.norm(y1) <= 1e-8 * kappa
+
+
+def _rank_M(rank, world, port, case, s_draws, out_dir):
+    import datetime
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import oracle
+    import workloads as W
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
+    mat = CASES[case][1](W)
+    smp = oracle.Sample(mat, seed=17, s=s_draws)
+    m, n = smp.mat.m, smp.mat.n
+    bounds = [m * r // world for r in range(world + 1)]
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    A = mat["A"] if mat["kind"] == "dense" else W.dense_from_csr(mat)
+    # the draws this rank owns, as rows with their counts
+    rows, counts = np.unique(smp.idx[(smp.idx >= r0) & (smp.idx < r1)], return_counts=True)
+    Wd = float(smp.W)
+    p = np.array([float(int(smp.w_hi[i]) << 64 | int(smp.w_lo[i])) for i in rows]) / Wd
+    Ahat = A[rows] / smp.d
+    M_r = (Ahat * (counts / (smp.s * p))[:, None]).T @ Ahat
+    t = torch.from_numpy(np.ascontiguousarray(M_r))
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    M = t.numpy().copy()
+    fixed = np.flatnonzero(np.diag(M) == 0.0)
+    M[fixed, fixed] = 1.0
+    dist.barrier()
+    dist.destroy_process_group()
+    np.save(os.path.join(out_dir, f"M{rank}.npy"), M)
+    with open(os.path.join(out_dir, f"own{rank}.txt"), "w") as f:
+        f.write(f"{int(counts.sum())} {fixed.size}\n")
+    if rank == 0:
+        Mo = oracle.SampledM(smp)
+        np.save(os.path.join(out_dir, "M_single.npy"), Mo.dense())
+        with open(os.path.join(out_dir, "single.txt"), "w") as f:
+            f.write(f"{smp.s} {Mo.n_fixed_diag}\n")
+
+
+@pytest.mark.parametrize("case,s_draws", [("dense_gauss_3001x40", None), ("csr_5000x300", None),
+                                          ("csr_5000x300", 150)])
+def test_sharded_normal_matrix_matches_one_process(tmp_path, case, s_draws):
+    """With 150 draws most columns of the CSR matrix are never sampled: their diagonal is
+    fixed to 1 once, after the sum, and a column that only another rank sampled keeps
+    that rank's value."""
+    import torch.multiprocessing as mp
+    world = CASES[case][0]
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_M, args=(r, world, port, case, s_draws, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(240)
+        assert p.exitcode == 0
+    Ms = [np.load(tmp_path / f"M{r}.npy") for r in range(world)]
+    for r in range(1, world):
+        assert np.array_equal(Ms[r], Ms[0])          # the all-reduced M is the same on every rank
+    owns = [open(tmp_path / f"own{r}.txt").read().split() for r in range(world)]
+    s, n_fixed = (int(v) for v in open(tmp_path / "single.txt").read().split())
+    assert sum(int(o[0]) for o in owns) == s          # every draw is summed by exactly one rank
+    assert all(int(o[1]) == n_fixed for o in owns)
+    assert (n_fixed > 0) == (s_draws is not None)
+    M1 = np.load(tmp_path / "M_single.npy")
+    assert np.array_equal(Ms[0] != 0.0, M1 != 0.0)   # the same pattern
+    assert np.max(np.abs(Ms[0] - M1)) <= 1e-13 * np.max(np.abs(M1))

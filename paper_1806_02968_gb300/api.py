@@ -335,7 +335,8 @@ def set_wait_limit(max_polls: int = 0):
 
 
 def set_sweep_form(form: int = 0):
-    """Form of the one-column sparse sweeps: 0 by shape, 1 grid, 2 one CTA, 3 one cluster."""
+    """Form of the sparse sweeps (lsq_set_sweep_form): 0 by shape, 1 grid, 2 one CTA, 3 one
+    cluster; RHS blocks take only form 3, where their n x k vector fits."""
     _check(L.load().lsq_set_sweep_form(int(form)), "lsq_set_sweep_form")
 
 

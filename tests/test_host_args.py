@@ -191,3 +191,20 @@ def test_wait_limit_argument_checks(lsq):
         assert e.value.code == 1
     lsq.set_wait_limit(1 << 31)
     lsq.set_wait_limit(0)
+
+
+def test_sweep_form_argument_checks(lsq):
+    """lsq_set_sweep_form takes 0 (by shape) to 3 (cluster); it only stores the setting."""
+    for bad in (-1, 4, 100):
+        with pytest.raises(lsq.L.LsqError) as e:
+            lsq.set_sweep_form(bad)
+        assert e.value.code == 1
+        assert "form must be" in _err(lsq)
+    for good in (1, 2, 3, 0):
+        lsq.set_sweep_form(good)
+
+
+def test_latency_probe_rejects_null_output(lsq):
+    L = lsq.L.load()
+    assert L.lsq_measure_latency(None, None) == 1
+    assert "out_ns" in _err(lsq)

@@ -209,6 +209,20 @@ def test_sampled_normal_matrix_is_unbiased(orc):
     assert np.all(np.abs(mean - N) <= 5 * se + 1e-12)
 
 
+def test_uniform_sampled_normal_matrix_is_unbiased(orc):
+    """The same expectation under the uniform density of Sec. 3.1 (p_i = 1/m): each draw is
+    weighted m/s, and the mean over 400 seeds must still be Â^T Â.  A uniform M that kept
+    the norm-squared weights 1/(s p_i) for the drawn rows, or dropped the factor m, fails."""
+    A = W.gaussian_dense(30, 4, 2)["A"] * np.linspace(0.2, 3, 30)[:, None]
+    mat = {"kind": "dense", "A": A}
+    Ah = A / np.linalg.norm(A, axis=0)
+    N = Ah.T @ Ah
+    reps = [orc.SampledM(orc.Sample(mat, seed=sd, s=12, sampling="uniform")).dense() for sd in range(400)]
+    mean = np.mean(reps, axis=0)
+    se = np.std(reps, axis=0) / np.sqrt(len(reps))
+    assert np.all(np.abs(mean - N) <= 5 * se + 1e-12)
+
+
 def test_spectral_error_within_the_paper_bound(orc):
     """Sec. 3.2, the approximation theorem: for ||Â||_F^2 = n, eps and delta in (0, 1),
     C = (2/3)(6 ||Â||^2 + 2 eps)(1 - log_n(delta / 2)) and s = C eps^-2 n log n give

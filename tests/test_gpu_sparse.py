@@ -102,6 +102,11 @@ def test_sparse_f32_values_with_f64_refinement(lsq, orc):
     xs, b = W.rhs_for(seen, 1, 1e-3, 9)
     X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b[0]).cuda(), o)
     assert info.converged[0] == 1 and info.relres_true[0] <= o.tol
+    # against the oracle's FP64 solve of the same (FP32-rounded) matrix: both meet the
+    # normal equation to tol, so their difference does in the Â^T Â norm
+    y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[0], tol=o.tol, maxit=o.maxit, max_outer=20)
+    assert oi["converged"] == 1
+    assert _same_solution(seen, smp.d, X.cpu().numpy(), y, b[0], o.tol)
 
 
 @pytest.mark.parametrize("device_loop", [0, 1])
@@ -217,8 +222,12 @@ def test_sparse_block_f32_refinement(lsq, orc):
     o.inner_tol = 1e-4
     xs, b = W.rhs_for(seen, 4, 1e-3, 19)
     X, info = lsq.lsq_pcg_solve(Mx, P, torch.from_numpy(b).cuda(), o)
+    X = X.cpu().numpy()
     for c in range(4):
         assert info.converged[c] == 1 and info.relres_true[c] <= o.tol
+        y, oi = orc.pcg(smp.mat, smp.d, Mo, b=b[c], tol=o.tol, maxit=o.maxit, max_outer=20)
+        assert oi["converged"] == 1
+        assert _same_solution(seen, smp.d, X[c], y, b[c], o.tol)
 
 
 @pytest.mark.parametrize("case,k", [("mid", 4), ("sprand", 3), ("wide", 2)])

@@ -105,3 +105,45 @@ def test_sweep_latency_bound_arithmetic():
     assert abs(out["bound_ms_per_sweep"] - 1583 * (160.0 + 150.0) / 1e6) < 1e-12
     assert abs(out["frac"] - out["bound_ms_per_sweep"] / out["ms_per_sweep"]) < 1e-12
     assert out["bound"] == "latency" and out["levels"] == 1583
+
+
+def test_paper_tables_match_the_golden_printed_counts():
+    """The printed iteration counts the GPU paper-tables run sets its results beside (Sec. 5.1
+    and 5.2) are the ones the oracle's pins use (tests/golden/paper_iterations.txt): CG's
+    count and RS's mean over ten runs, row by row."""
+    sys.path.insert(0, ROOT)
+    import bench
+    gold = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_iterations.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            fam, n, m, it_cg, it_rs, rs_mean, rs_std = line.split()
+            gold[(fam, int(m), int(n))] = (int(it_cg), float(rs_mean))
+    for fam, key in (("gaussian", "gauss"), ("semi_gaussian", "semi")):
+        rows = bench.PAPER_TABLES[fam]
+        assert len(rows) == 5
+        for (m, n), cg, rs in rows:
+            assert gold[(key, m, n)] == (cg, rs), (fam, m, n)
+
+
+def test_paper_tables_of_the_ill_conditioned_families_match_the_printed_counts():
+    """The UDV (Sec. 5.4) and random graph Laplacian (Sec. 5.5) rows of the GPU paper-tables
+    run against tests/golden/paper_iterations_udv_graph.txt: the printed kappa(A^T A) of each
+    UDV matrix, the graph sizes (two Chung-Lu graphs of n vertices glued on 5 give 2 n - 5,
+    the printed vertex counts up to one), CG's count and RS's ten-run mean."""
+    sys.path.insert(0, ROOT)
+    import bench
+    gold = {"udv": [], "graph": []}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_iterations_udv_graph.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            fam, key, m, n, it_cg, it_rs, rs_mean, rs_std = line.split()
+            gold[fam].append((float(key), int(it_cg), float(rs_mean)))
+    udv = bench.PAPER_TABLES["udv_linear_90000x300"]
+    assert [(float(k), cg, float(rs)) for k, cg, rs in udv] == gold["udv"]
+    graph = bench.PAPER_TABLES["graph_laplacian_chung_lu"]
+    assert len(graph) == len(gold["graph"]) == 5
+    for (n_each, cg, rs), (verts, g_cg, g_rs) in zip(graph, gold["graph"]):
+        assert abs((2 * n_each - 5) - verts) <= 1 and (cg, float(rs)) == (g_cg, g_rs)

@@ -33,6 +33,10 @@ MUTANTS = [
      "        acc += ((u128)w_hi[i] << 64) | w_lo[i];\n",
      "        acc += ((u128)w_hi[i] << 64) | w_lo[i];\n        P_lo[i] = (uint64_t)acc;\n"
      "        P_hi[i] = (uint64_t)(acc >> 64);\n"),
+    ("draw_words_swapped", "Alg. 1: the 128-bit uniform is word1 * 2^64 + word0",
+     "u128 U = ((u128)r[1] << 64) | r[0];", "u128 U = ((u128)r[0] << 64) | r[1];"),
+    ("M_scale_wrong_column", "Sec. 3.3: entry (j, c) of a draw's outer product is a_ij a_ic / (d_j d_c)",
+     "acc[c] += coef * (v[k] / d[c]);", "acc[c] += coef * (v[k] / d[j]);"),
     ("M_scale_drops_s", "Sec. 3.3: each draw is scaled by 1 / (s p_i)",
      "gam[t] = 1.0 / ((double)s * p);", "gam[t] = 1.0 / p;"),
     ("M_unnormalised_column", "Sec. 3.3: M is built from the normalised rows a_i D^{-1}",

@@ -49,6 +49,10 @@ MUTANTS = [
     ("sgs_backward_lower_triangle", "Alg. 3: the backward sweep uses B^T, the upper triangle",
      "if (M->col[q] > j) acc -= M->val[q] * del[M->col[q]];",
      "if (M->col[q] < j) acc -= M->val[q] * del[M->col[q]];"),
+    ("sgs_backward_runs_forward", "Alg. 3: the backward correction is a back substitution, row n-1 first",
+     "for (int64_t j = n - 1; j >= 0; --j) {", "for (int64_t j = 0; j < n; ++j) {"),
+    ("sgs_correction_replaces_e", "Alg. 3: each correction is added to e",
+     "for (int64_t j = 0; j < n; ++j) e[j] += del[j];", "for (int64_t j = 0; j < n; ++j) e[j] = del[j];"),
     ("sgs_residual_sign", "Alg. 3: the correction solves for r - M e",
      "res[j] = r[j] - acc;", "res[j] = r[j] + acc;"),
     ("apply_A_unnormalised", "Sec. 4.2: q = A D^{-1} p",

@@ -26,6 +26,8 @@ MUTANTS = [
      "double u = t * inv_d2[row_col(A, i, k)];", "double u = t;"),
     ("philox_key_word", "Philox4x64-10 (Salmon et al.): key word k0 enters n0",
      "uint64_t n0 = hi1 ^ c1 ^ k0,", "uint64_t n0 = hi1 ^ c1 ^ k1,"),
+    ("philox_nine_rounds", "Philox4x64-10 (Salmon et al.): ten rounds",
+     "for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {"),
     ("philox_weyl_constant", "Philox4x64-10: Weyl constant of the first key word",
      "W0 = 0x9E3779B97F4A7C15ull", "W0 = 0x9E3779B97F4A7C17ull"),
     ("prefix_inclusive", "Alg. 1: the search runs over the exclusive prefix",
@@ -57,6 +59,8 @@ MUTANTS = [
      "res[j] = r[j] - acc;", "res[j] = r[j] + acc;"),
     ("apply_A_unnormalised", "Sec. 4.2: q = A D^{-1} p",
      "acc += (v[k] / d[j]) * p[j];", "acc += v[k] * p[j];"),
+    ("apply_A_times_d", "Sec. 4.2: q = A D^{-1} p divides by the column scale",
+     "acc += (v[k] / d[j]) * p[j];", "acc += (v[k] * d[j]) * p[j];"),
     ("apply_AT_wrong_operand", "Sec. 4.2: w = D^{-1} A^T q, entry (i, j) times q_i",
      "w[j] += (v[k] / d[j]) * q[i];", "w[j] += (v[k] / d[j]) * q[i] * (i % 2 ? 1.0 : -1.0);"),
     ("pcg_residual_sign", "Alg. 2 step 4: g <- g - alpha A^T A p",

@@ -31,6 +31,19 @@ def pytest_collection_modifyitems(config, items):
 
 @pytest.fixture(scope="session")
 def orc():
+    pkg = os.environ.get("LSQ_ORACLE_PKG")
+    if pkg:
+        # a copy of the oracle package with one planted mistake in its Python layer
+        # (tests/test_oracle_mutants.py): the pins run against it and must fail
+        import importlib.util
+        here = os.path.join(pkg, "oracle")
+        spec = importlib.util.spec_from_file_location("oracle", os.path.join(here, "__init__.py"),
+                                                      submodule_search_locations=[here])
+        mod = importlib.util.module_from_spec(spec)
+        sys.modules["oracle"] = mod
+        spec.loader.exec_module(mod)
+        mod.build()
+        return mod
     import oracle
     mutant = os.environ.get("LSQ_ORACLE_MUTANT")
     if mutant:

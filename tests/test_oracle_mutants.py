@@ -14,6 +14,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lsq_oracle.c")
+PY = os.path.join(ROOT, "oracle", "__init__.py")
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
 # (id, step of the paper, text in the oracle, planted replacement)
@@ -121,4 +122,49 @@ def test_pins_catch_planted_mistake(tmp_path, mid, step, old, new):
     out = _run_pins(_build(tmp_path, text.replace(old, new)))
     # 1: a pin failed.  A crash of the copy (negative: killed by a signal) also counts as
     # caught; 2-5 (interrupted, internal or usage error, nothing collected) do not.
+    assert out.returncode == 1 or out.returncode < 0, (mid, step, out.returncode, out.stdout[-1500:])
+
+
+# Mistakes in the oracle's Python layer (oracle/__init__.py): the steps it computes itself
+# rather than in C.  (id, step of the paper, text, planted replacement)
+PY_MUTANTS = [
+    ("solve_x_times_d", "Alg. 2: x = D^{-1} y", "self.x = y / self.smp.d", "self.x = y * self.smp.d"),
+    ("adjoint_rhs_times_d", "adjoint: A^T A lam = G is solved as Â^T Â mu = D^{-1} G",
+     "h=np.asarray(G, np.float64) / d", "h=np.asarray(G, np.float64) * d"),
+    ("adjoint_lam_times_d", "adjoint: lam = D^{-1} mu", "lam = mu / d", "lam = mu * d"),
+    ("adjoint_dense_sign", "adjoint: dL/dA = r lam^T - (A lam) x^T",
+     "gA = np.outer(r, lam) - np.outer(Alam, x)", "gA = np.outer(r, lam) + np.outer(Alam, x)"),
+    ("adjoint_csr_operand", "adjoint: dL/dA_ij = r_i lam_j - (A lam)_i x_j",
+     "gv = r[rows] * lam[cols] - Alam[rows] * x[cols]", "gv = r[rows] * lam[cols] - Alam[rows] * x[rows % x.size]"),
+    ("uniform_keeps_norm2", "Sec. 3.1: uniform sampling gives every row the same weight",
+     "self.w_lo = np.ones(self.mat.m, np.uint64)", "self.w_lo, _ = row_weights(self.mat, self.inv_d2)"),
+]
+
+
+def _run_pins_py(pkg_dir):
+    env = dict(os.environ, LSQ_ORACLE_PKG=str(pkg_dir), PYTHONDONTWRITEBYTECODE="1")
+    env.pop("LSQ_ORACLE_MUTANT", None)
+    return subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider",
+                           "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
+def _copy_package(tmp_path, py_text):
+    d = tmp_path / "oracle"
+    d.mkdir()
+    (d / "lsq_oracle.c").write_text(open(SRC).read())
+    (d / "__init__.py").write_text(py_text)
+    return tmp_path
+
+
+def test_pins_pass_on_the_oracle_package_copied(tmp_path):
+    """The Python harness itself: an unmodified copy of the package passes every pin."""
+    out = _run_pins_py(_copy_package(tmp_path, open(PY).read()))
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
+
+
+@pytest.mark.parametrize("mid,step,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_catch_planted_mistake_in_the_python_layer(tmp_path, mid, step, old, new):
+    text = open(PY).read()
+    assert text.count(old) == 1, f"{mid}: the planted text must occur once in the oracle"
+    out = _run_pins_py(_copy_package(tmp_path, text.replace(old, new)))
     assert out.returncode == 1 or out.returncode < 0, (mid, step, out.returncode, out.stdout[-1500:])

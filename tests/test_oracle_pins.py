@@ -530,6 +530,40 @@ def test_adjoint_matches_closed_form_and_finite_differences(orc):
         assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))
 
 
+def test_csr_adjoint_equals_the_dense_gradient_on_the_stored_entries(orc):
+    """The CSR form of the adjoint returns dL/dA only at A's stored entries: those must be
+    the entries of the dense closed form r lam^T - (A lam) x^T (pinned above) for the same
+    matrix, and dL/db and lam must be the dense ones."""
+    mat = W.sparse_random(400, 12, 4, 5)
+    A = W.dense_from_csr(mat)
+    xs, b = W.rhs_for(mat, 1, 1e-1, 3)
+    b = b[0]
+    S = orc.Solve(mat, b, seed=2, tol=1e-14)
+    G = 2 * (S.x - np.random.default_rng(1).standard_normal(12))
+    gb, gv, lam, info = orc.adjoint(mat, S.smp, S.M, S.x, b, G, tol=1e-14)
+    lam_ref = np.linalg.solve(A.T @ A, G)
+    np.testing.assert_allclose(lam, lam_ref, rtol=1e-9)
+    np.testing.assert_allclose(gb, A @ lam_ref, rtol=1e-9, atol=1e-12)
+    r = b - A @ S.x
+    gA = np.outer(r, lam_ref) - np.outer(A @ lam_ref, S.x)
+    rows = np.repeat(np.arange(400), np.diff(mat["row_ptr"]))
+    np.testing.assert_allclose(gv, gA[rows, mat["col_idx"]], rtol=1e-8, atol=1e-12)
+    # and central finite differences in three stored values
+    target = S.x - G / 2
+
+    def loss(vals):
+        m2 = dict(mat)
+        m2["vals"] = vals
+        return np.sum((orc.Solve(m2, b, seed=2, tol=1e-14).x - target) ** 2)
+
+    h = 1e-6
+    for q in (0, 517, mat["vals"].size - 1):
+        e = np.zeros_like(mat["vals"])
+        e[q] = h
+        fd = (loss(mat["vals"] + e) - loss(mat["vals"] - e)) / (2 * h)
+        assert abs(fd - gv[q]) <= 1e-6 * max(1.0, abs(gv[q])), (q, fd, gv[q])
+
+
 # ---------------------------------------------------------------------------------------
 # Sec. 5.1-5.2: the iteration counts the paper prints for its well-conditioned examples.
 # The paper does not state b; a standard normal b is used.  CG on the normalised A is a

@@ -649,6 +649,27 @@ def test_uniform_sampling_misses_the_rows_of_a_coherent_matrix(orc):
     assert np.abs(Mn.dense() - np.eye(n)).max() < 1.0 < np.abs(Mu.dense() - np.eye(n)).max()
 
 
+def test_uniform_sampling_on_the_semi_gaussian_identity_block(orc):
+    """Sec. 5.2's [B 0; 0 I] under uniform draws (p_i = 1/m): an identity column j is touched
+    only by its own row, so row j of A_s^T A_s is c_j m / s on the diagonal and zero elsewhere
+    (c_j = times that row was drawn), and a column never drawn gets the replaced diagonal 1,
+    which is exactly its entry of Â^T Â."""
+    m, n = 3000, 40
+    h = n // 2
+    mat = W.semi_gaussian_dense(m, n, 21)
+    smp = orc.Sample(mat, seed=7, sampling="uniform")
+    M = orc.SampledM(smp).dense()
+    first = m - (n - h)                        # the identity rows are the last n - h
+    counts = np.bincount(smp.idx, minlength=m)[first:]
+    assert (counts == 0).sum() >= 1 and (counts > 0).sum() >= 1
+    for k in range(n - h):
+        j = h + k
+        want = 1.0 if counts[k] == 0 else counts[k] * m / smp.s
+        assert M[j, j] == pytest.approx(want, rel=1e-14)
+        assert np.count_nonzero(M[j]) == 1 and np.count_nonzero(M[:, j]) == 1
+    assert orc.SampledM(smp).n_fixed_diag == int((counts == 0).sum())
+
+
 def test_uniform_sampling_is_a_weaker_preconditioner_when_rows_differ(orc):
     """Sec. 3.1 on a matrix whose columns are carried by a few rows (400 Gaussian rows of
     20000; the rest scaled by 1e-3): PCG with the norm-squared density converges in a
